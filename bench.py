@@ -1,0 +1,401 @@
+"""Benchmark of the EVP ternary search hot path on one GB300.
+
+Workload (defaults): a resident database of 10,000,000 l2-normalised
+Gaussian-mixture embeddings, d = 768 (1,024 centres, anisotropic scales),
+encoded once at x = 512 (packed codes 1.92 GB; float32 originals 30.7 GB
+kept for the rerank).  One step = one batch of 1,024 float32 queries through
+the whole path: evp_encode -> ternary_knn (shortlist of 100 by Delta) ->
+rerank (best 10 by float32 scalar product).  Inputs are larger than L2, so
+no flush is needed between steps.
+
+Prints one JSON line.  `--impl reference` times the CPU oracle instead (a
+bounded sample of the same workload, scaled to the full database).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "queries/s at 10Mx768 ternary (encode + scan + rerank), recall@10"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--d", type=int, default=768)
+    ap.add_argument("--x", type=int, default=0, help="0 = default x (2d/3 rule)")
+    ap.add_argument("--batch", type=int, default=1024)
+    ap.add_argument("--shortlist", type=int, default=100)
+    ap.add_argument("--k", type=int, default=10)
+    ap.add_argument("--centres", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-recall", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return j.get("hbm_gbs", 6800.0), j.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# POPC issue rate measured on this GB300 (16 per clock per SM) at the
+# maximum SM clock, for the integer-pipe roofline of the popcount scan.
+POPC_PER_CLK_PER_SM = 16
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"evp_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(U_dev, Q_host, x, shortlist, k, n_total, n_rows=200_000, n_q=8):
+    """Time the oracle as it stands (single thread) on a bounded sample:
+    n_q queries encoded, scanned exhaustively over n_rows database rows,
+    and re-ranked; the scan part is scaled to the full database."""
+    import concurrent.futures as cf
+    import oracle
+    import torch
+    rows = U_dev[:n_rows].cpu().numpy()
+    # encoding the sample database is pre-processing (untimed), spread over threads
+    chunks = np.array_split(np.arange(n_rows), os.cpu_count() or 1)
+    Vs = np.empty(rows.shape, dtype=np.int8)
+
+    def job(ix):
+        if len(ix):
+            Vs[ix[0]:ix[-1] + 1] = oracle.encode(rows[ix[0]:ix[-1] + 1], x)
+
+    with cf.ThreadPoolExecutor(len(chunks)) as ex:
+        list(ex.map(job, chunks))
+    Qs = Q_host[:n_q]
+    t0 = time.perf_counter()
+    Vq = oracle.encode(Qs, x)
+    t1 = time.perf_counter()
+    ids, _ = oracle.knn(Vq, Vs, shortlist)
+    t2 = time.perf_counter()
+    oracle.rerank(Qs, rows, ids, k)
+    t3 = time.perf_counter()
+    scale = n_total / n_rows
+    per_query = ((t1 - t0) + (t2 - t1) * scale + (t3 - t2)) / n_q
+    del torch
+    return 1.0 / per_query, {
+        "sample": f"{n_q} queries over the first {n_rows} database rows "
+                  f"(scan time scaled x{scale:.0f} to {n_total} rows); encode+knn+rerank",
+        "seconds": t3 - t0}
+
+
+def main_reference(a):
+    """CPU oracle on the same workload, one bounded sample per step."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2506_00528_gb300 import synth
+    d = a.d
+    x = a.x or (2 * d + 1) // 3
+    n_rows = min(a.n, 100_000)
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    U = synth.mixture_torch(n_rows, d, n_centres=a.centres, anisotropic=True,
+                            stream=synth.STREAM_DB, device=dev)
+    Qh = synth.mixture_torch(64, d, n_centres=a.centres, anisotropic=True,
+                             stream=synth.STREAM_QUERIES, device=dev).cpu().numpy()
+    vals = []
+    samp = None
+    for i in range(a.warmup + a.steps):
+        v, info = cpu_oracle_sample(U, Qh, x, a.shortlist, a.k, a.n, n_rows=n_rows, n_q=2)
+        samp = info["sample"]
+        if i >= a.warmup:
+            vals.append(v)
+    value = float(np.median(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1000.0 * a.batch / value, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int8 ternary / f64", "data": "synthetic",
+        "config": {"workload": f"{a.n}x{d} ternary kNN, x={x}, batch {a.batch}, "
+                               f"shortlist {a.shortlist}, k={a.k}"},
+        "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
+                         "sample": samp},
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return main_reference(a)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2506_00528_gb300 import build as _build
+    from paper_2506_00528_gb300 import evp, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    evp.load()
+
+    d, B, n, n_sl, k = a.d, a.batch, a.n, a.shortlist, a.k
+    x = a.x or evp.default_x(d)
+    W = evp.words(d)
+    # ---- resident database (replicas only: every rank holds the same one)
+    U = synth.mixture_torch(n, d, n_centres=a.centres, anisotropic=True,
+                            stream=synth.STREAM_DB, device=dev)
+    st = evp.new_status(dev)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    S = evp.encode(U, x, status=st)
+    t1.record()
+    torch.cuda.synchronize()
+    evp.check_status(st, "database encode")
+    db_encode_ms = t0.elapsed_time(t1)
+    # ---- query batches: distinct per step (cycled pool of 8)
+    pool = 8
+    Qall = synth.mixture_torch(pool * B, d, n_centres=a.centres, anisotropic=True,
+                               stream=synth.STREAM_QUERIES + 10 * rank, device=dev)
+    Qb = [Qall[i * B:(i + 1) * B] for i in range(pool)]
+    Tq = torch.empty((B, 2 * W), dtype=torch.int64, device=dev)
+    sl = torch.empty((B, n_sl), dtype=torch.int64, device=dev)
+    sd = torch.empty((B, n_sl), dtype=torch.int32, device=dev)
+    ws = torch.empty(evp.knn_workspace_bytes(B, n, d, n_sl), dtype=torch.uint8, device=dev)
+    rid = torch.empty((B, k), dtype=torch.int64, device=dev)
+    rsc = torch.empty((B, k), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(Q):
+        evp.encode(Q, x, out=Tq, status=st, stream=stream)
+        evp.ternary_knn(Tq, S, d, x, n_sl, ids=sl, dist=sd, ws=ws, status=st, stream=stream)
+        evp.rerank(Q, U, sl, k, ids=rid, scores=rsc, status=st, stream=stream)
+
+    for i in range(a.warmup):
+        step(Qb[i % pool])
+    torch.cuda.synchronize()
+    evp.check_status(st, "warmup")
+
+    # ---- device-resident timing
+    sampler = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    evp.timing_reset()
+    evp.timing_enable(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(a.steps):
+        step(Qb[i % pool])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    evp.timing_enable(False)
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    per_kernel = {name: evp.timing_read(name) for name in
+                  ("encode", "scan_init", "scan_popc", "final_merge", "rerank")}
+    evp.check_status(st, "timed steps")
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / a.steps
+    value = world * B * a.steps / (ms / 1000.0)
+
+    # ---- end to end through the API with host buffers (pinned)
+    Qh = [q.cpu().pin_memory() for q in Qb]
+    Qd = torch.empty((B, d), dtype=torch.float32, device=dev)
+    ids_h = torch.empty((B, k), dtype=torch.int64).pin_memory()
+    sc_h = torch.empty((B, k), dtype=torch.float32).pin_memory()
+    for i in range(a.warmup):
+        Qd.copy_(Qh[i % pool], non_blocking=True)
+        step(Qd)
+        ids_h.copy_(rid, non_blocking=True)
+        sc_h.copy_(rsc, non_blocking=True)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0.record(stream)
+    for i in range(a.steps):
+        Qd.copy_(Qh[i % pool], non_blocking=True)
+        step(Qd)
+        ids_h.copy_(rid, non_blocking=True)
+        sc_h.copy_(rsc, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * B * a.steps / (e2e_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel (the popcount scan)
+    hbm_peak, bf16_peak, peak_src = load_peaks()
+    n_scan, scan_ms = per_kernel["scan_popc"]
+    scan_avg_ms = scan_ms / max(1, n_scan)
+    # algorithmic work per scan launch: one pass over the database codes for
+    # up to 16 queries; per (query, row) pair 4W 32-bit popcounts.
+    passes_per_step = (B + 15) // 16
+    pairs_per_launch = n * (B / passes_per_step)
+    popc_per_launch = pairs_per_launch * 4 * W
+    bytes_per_launch = n * 16 * W
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    popc_peak = POPC_PER_CLK_PER_SM * sm_count * 2070e6
+    roofline = {
+        "kernel": "scan_popc",
+        "bound": "alu",
+        "achieved": popc_per_launch / (scan_avg_ms / 1e3) / 1e12,
+        "peak": popc_peak / 1e12,
+        "unit": "Tpopc/s",
+        "frac": (popc_per_launch / (scan_avg_ms / 1e3)) / popc_peak,
+        "traffic": None,
+        "hbm_achieved_gbs": bytes_per_launch / (scan_avg_ms / 1e3) / 1e9,
+        "hbm_peak_gbs": hbm_peak,
+        "peak_source": f"POPC 16/clk/SM (probe) x {sm_count} SMs x 2070 MHz; HBM {peak_src}",
+        "launches": n_scan, "avg_ms": scan_avg_ms,
+    }
+    kernels = {nm: {"launches": c, "total_ms": round(t, 3)} for nm, (c, t) in per_kernel.items()}
+
+    # ---- recall@10 against exact float32 cosine kNN (first 64 queries)
+    recall = None
+    if not a.no_recall:
+        torch.backends.cuda.matmul.allow_tf32 = False
+        nrq = min(64, B)
+        Qr = Qb[0][:nrq]
+        step(Qb[0])
+        torch.cuda.synchronize()
+        best_s = torch.full((nrq, k), -float("inf"), device=dev)
+        best_i = torch.zeros((nrq, k), dtype=torch.int64, device=dev)
+        for c0 in range(0, n, 1 << 20):
+            s = Qr @ U[c0:c0 + (1 << 20)].T
+            v, i = torch.topk(s, k, dim=1)
+            cat_s = torch.cat([best_s, v], 1)
+            cat_i = torch.cat([best_i, i + c0], 1)
+            best_s, j = torch.topk(cat_s, k, dim=1)
+            best_i = torch.gather(cat_i, 1, j)
+        truth = best_i.cpu().numpy()
+        got_rr = rid[:nrq].cpu().numpy()
+        got_tern = sl[:nrq, :k].cpu().numpy()
+        recall = {
+            "rerank_10_at_100": float(np.mean([len(set(a_) & set(b_)) / k
+                                               for a_, b_ in zip(got_rr, truth)])),
+            "ternary_10_at_10": float(np.mean([len(set(a_) & set(b_)) / k
+                                               for a_, b_ in zip(got_tern, truth)])),
+            "queries": nrq}
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        v, info = cpu_oracle_sample(U, Qb[0][:8].cpu().numpy(), x, n_sl, k, n)
+        cpu = {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": info["sample"]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64 bitplanes / int32 Delta / f32 rerank", "data": "synthetic",
+            "config": {"workload": f"{n}x{d} ternary kNN (Gaussian mixture, {a.centres} centres, "
+                                   f"anisotropic), x={x}, batch {B} queries/step, shortlist "
+                                   f"{n_sl} by Delta, rerank to k={k}",
+                       "n": n, "d": d, "x": x, "batch": B, "shortlist": n_sl, "k": k,
+                       "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (codes 1.92 GB, floats 30.7 GB); no flush"},
+            "scanned_gbs_logical": B * n * 16 * W / (ms_per_step / 1e3) / 1e9,
+            "db_encode": {"rows": n, "ms": db_encode_ms,
+                          "gbs": n * (4 * d + 16 * W) / (db_encode_ms / 1e3) / 1e9},
+            "roofline": roofline,
+            "kernels": kernels,
+            "recall_at_10": recall,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "queries/s",
+                    "h2d_bytes_per_step": B * d * 4, "d2h_bytes_per_step": B * k * 12},
+            "gpu_launches": sum(c for c, _ in per_kernel.values()),
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

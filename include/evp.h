@@ -1,0 +1,191 @@
+/*
+ * evp.h -- C ABI of libevp, a GB300 (sm_103a) implementation of the search
+ * hot path of "Ultra-Quantisation: Efficient Embedding Search via 1.58-bit
+ * Encodings" (Connor, Dearle, Claydon; arXiv 2506.00528).
+ *
+ * The path: float32 embeddings are mapped to their nearest {x,d}
+ * Equi-Voronoi-Polytope vertex (a ternary vector with exactly x non-zeros,
+ * Sec. 2.3-2.4) stored as two bitplanes (Sec. 5.1.2); a query batch is
+ * compared exhaustively with a database of such codes using the integer
+ * proxy distance Delta (notation table, Sec. 2.6); the k nearest are kept
+ * per query; optionally a shortlist is re-ordered by the original float
+ * vectors (Sec. 5.3).
+ *
+ * Conventions shared by every call:
+ *  - Array arguments are DEVICE pointers owned by the caller unless stated
+ *    otherwise.  The library keeps no pointer after a call returns (except
+ *    inside an evp_db_t, which borrows its arrays until evp_db_destroy).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream: they enqueue kernels
+ *    and return.
+ *  - Argument errors are detected on the host, returned immediately, and
+ *    nothing is launched.  Errors that depend on the data (non-finite
+ *    inputs, out-of-range shortlist ids, a device wait that timed out) are
+ *    written to *dev_status, a device int32 that the caller sets to 0
+ *    beforehand and reads after synchronising the stream; the first error
+ *    written wins.  dev_status may be NULL, in which case such errors are
+ *    not reported.  Outputs are unspecified when any status is not EVP_OK.
+ *  - All entry points are safe to call from several host threads on
+ *    different streams; calls that share an output or workspace buffer
+ *    must be ordered by the caller.
+ *
+ * Packed code layout (the boundary format).  W = ceil(d/64).  One code is
+ * 2W uint64 words, row-major, one row per vector: words [0, W) hold the
+ * v+ plane (bit set where the element is +1) and words [W, 2W) the v-
+ * plane (bit set where the element is -1).  Dimension j is bit (j mod 64)
+ * of word floor(j/64) of its plane.  Bits at j >= d are 0.  Database
+ * arrays passed to ternary_knn must be 16-byte aligned.
+ */
+#ifndef EVP_H
+#define EVP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    EVP_OK = 0,
+    EVP_ERR_INVALID = 1,     /* bad argument (host-detected)                  */
+    EVP_ERR_NONFINITE = 2,   /* NaN or infinity in a float input              */
+    EVP_ERR_NO_MEMORY = 3,   /* workspace too small / allocation refused      */
+    EVP_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up            */
+    EVP_ERR_CUDA = 5,        /* a CUDA runtime call failed                    */
+    EVP_ERR_UNSUPPORTED = 6, /* valid request outside this build's limits     */
+    EVP_ERR_RANGE = 7        /* an index argument lies outside its array      */
+} evp_status_t;
+
+/* Limits of this build. */
+#define EVP_MAX_D_ENCODE 2048   /* evp_encode: d <= 2048                       */
+#define EVP_MAX_D_SCAN   1024   /* ternary_knn: d <= 1024                      */
+#define EVP_MAX_K        1024   /* ternary_knn: k <= 1024                      */
+#define EVP_MAX_SHORTLIST 4096  /* rerank: n <= 4096                           */
+#define EVP_MAX_D_RERANK 4096   /* rerank: d <= 4096                           */
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* evp_status_string(int32_t status);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t evp_version(void);
+
+/* W = ceil(d/64): uint64 words per bitplane; a packed code has 2W words.
+ * Returns 0 for d < 1. */
+int32_t evp_words(int32_t d);
+
+/* The x of Sec. 5.1.1: the smallest x in [1, d] maximising the vertex count
+ * C(d,x) * 2^x, which is floor((2d+1)/3).  Returns 0 for d < 1. */
+int32_t evp_default_x(int32_t d);
+
+/* ---------------------------------------------------------------------
+ * evp_encode -- nearest {x,d} EVP vertex of each row (Sec. 2.4).
+ *
+ * For each row u of U the x elements of largest |u_i| are kept, +1 where
+ * u_i is not negative and -1 where u_i < 0, every other element 0
+ * (Sec. 2.4, steps 1-3), and the result is packed as above.
+ * Readings where the paper is silent: magnitudes compare by their IEEE-754
+ * bits with the sign cleared; equal magnitudes are taken lowest index
+ * first; a selected +0.0 or -0.0 becomes +1, so every code has exactly x
+ * non-zeros.  The float bytes are used as given (rows are expected to be
+ * l2-normalised, Sec. 1.1, but the code does not depend on the scale).
+ *
+ *   U          [n][d] float32, row-major, device.
+ *   n          rows, n >= 0 (n == 0 is a no-op).
+ *   d          1 <= d <= EVP_MAX_D_ENCODE.
+ *   x          1 <= x <= d.
+ *   T          [n][2W] uint64 output, device.
+ *   dev_status receives EVP_ERR_NONFINITE if any U element is NaN or
+ *              infinite (the affected codes are then unspecified).
+ * Returns EVP_OK, EVP_ERR_INVALID (null pointer with n > 0, d or x out of
+ * range), EVP_ERR_UNSUPPORTED (d > EVP_MAX_D_ENCODE) or EVP_ERR_CUDA.
+ * ------------------------------------------------------------------- */
+int32_t evp_encode(const float* U, int64_t n, int32_t d, int32_t x,
+                   uint64_t* T, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
+ * ternary_knn -- exhaustive k-nearest-neighbour scan in the proxy space.
+ *
+ * Delta(q, s) = ||q - s||^2 over the ternary vectors, which for two codes
+ * with x non-zeros each is 2x - 2*b2sp(q, s), with b2sp the bitplane
+ * scalar product of Sec. 5.1.2:
+ *   b2sp = bsp(q+,s+) + bsp(q-,s-) - bsp(q+,s-) - bsp(q-,s+),
+ *   bsp(a,b) = popcount(a AND b).
+ * Delta is even and lies in [0, 4x]; smaller is nearer.  For each query
+ * the k database rows with the smallest (Delta, row index) pairs are
+ * returned in ascending order: equal Delta is broken by the lower row
+ * index, so the result is unique (the exhaustive search of Sec. 5.3 and of
+ * the 100-query scans of Table 5).
+ *
+ *   Q          [nq][2W] packed query codes, device.
+ *   nq         queries, nq >= 0 (0 is a no-op).
+ *   S          [ns][2W] packed database codes, device, 16-byte aligned.
+ *   ns         1 <= ns < 2^31 rows.
+ *   d          1 <= d <= EVP_MAX_D_SCAN.
+ *   x          non-zeros per code, 1 <= x <= d (the same x for Q and S).
+ *   k          1 <= k <= min(ns, EVP_MAX_K).
+ *   ids        [nq][k] int64 output: database row indices.
+ *   dist       [nq][k] int32 output: Delta of each returned row.
+ *   ws         device workspace of at least ternary_knn_workspace(...)
+ *              bytes, 256-byte aligned; its contents on entry are ignored.
+ *   ws_bytes   size of ws.
+ * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_NO_MEMORY (ws_bytes too small),
+ * EVP_ERR_UNSUPPORTED (d > EVP_MAX_D_SCAN or k > EVP_MAX_K) or
+ * EVP_ERR_CUDA.  dev_status may receive EVP_ERR_TIMEOUT.
+ * ------------------------------------------------------------------- */
+size_t ternary_knn_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k);
+
+int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns,
+                    int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist,
+                    void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
+ * rerank -- re-order a shortlist by the original vectors (Sec. 5.3: n > k
+ * proxy results are re-ordered in the original space and the best k
+ * kept).
+ *
+ * score(q, s) = <q, s> in float32 (for l2-normalised rows this orders as
+ * cosine similarity and as Euclidean distance, Sec. 1.1), summed in a
+ * fixed order: per lane of a warp a running FMA over a strided share of
+ * the d elements, then a five-level butterfly over the 32 lanes.  Output
+ * per query: the k best entries by (score descending, row index
+ * ascending); -0.0 is treated as +0.0.
+ *
+ *   Q          [nq][d] float32 queries, device.
+ *   S          [ns][d] float32 database rows, device.
+ *   shortlist  [nq][n] int64 row ids; -1 marks an empty entry (skipped).
+ *   n          1 <= n <= EVP_MAX_SHORTLIST.
+ *   k          1 <= k <= n.
+ *   ids        [nq][k] int64 output; positions beyond the number of
+ *              non-empty entries get -1.
+ *   scores     [nq][k] float32 output; -infinity where ids is -1.
+ * dev_status receives EVP_ERR_RANGE for an id outside [-1, ns) (the entry
+ * is then skipped) and EVP_ERR_NONFINITE for a non-finite score.
+ * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_UNSUPPORTED (d or n above the
+ * limits) or EVP_ERR_CUDA.
+ * ------------------------------------------------------------------- */
+int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d,
+               const int64_t* shortlist, int32_t n, int32_t k,
+               int64_t* ids, float* scores, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Kernel timing (measurement support; the paper has no counterpart).
+ *
+ * evp_timing_enable(1) makes every later call record a pair of CUDA events
+ * on its stream around each launch of the library's kernels; (0) stops
+ * recording.  evp_timing_read synchronises on the recorded events and
+ * returns, for the kernel family `name` ("encode", "scan_init",
+ * "scan_popc", "final_merge", "rerank"), the number of launches and their total
+ * duration in milliseconds since the last evp_timing_reset.  Returns
+ * EVP_OK, EVP_ERR_INVALID (null outputs) or EVP_ERR_CUDA.  Enabling adds
+ * two event records per launch; leave it off outside measurements.
+ * ------------------------------------------------------------------- */
+int32_t evp_timing_enable(int32_t on);
+int32_t evp_timing_reset(void);
+int32_t evp_timing_read(const char* name, int64_t* launches, double* total_ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EVP_H */

@@ -1,0 +1,182 @@
+// C ABI entry points of libevp (declared in include/evp.h): argument
+// checks on the host, then kernel launches on the caller's stream.
+#include "evp_internal.cuh"
+
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+namespace evp {
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (cached[dev] == 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+// ---- kernel timing ------------------------------------------------------
+namespace {
+
+struct TimingRecord {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
+struct TimingState {
+    std::mutex mu;
+    bool enabled = false;
+    std::vector<TimingRecord> records;
+    std::vector<cudaEvent_t> spare;
+};
+
+TimingState& timing() {
+    static TimingState* t = new TimingState();  // never destroyed: safe at exit
+    return *t;
+}
+
+cudaEvent_t take_event(TimingState& t) {
+    if (!t.spare.empty()) {
+        cudaEvent_t e = t.spare.back();
+        t.spare.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+}  // namespace
+
+TimedLaunch::TimedLaunch(const char* name, cudaStream_t stream)
+    : name_(name), stream_(stream), slot_(-1) {
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> g(t.mu);
+    if (!t.enabled) return;
+    TimingRecord r{name, take_event(t), take_event(t)};
+    if (!r.start || !r.stop) return;
+    if (cudaEventRecord(r.start, stream) != cudaSuccess) return;
+    slot_ = (int)t.records.size();
+    t.records.push_back(r);
+}
+
+TimedLaunch::~TimedLaunch() {
+    if (slot_ < 0) return;
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> g(t.mu);
+    if (slot_ < (int)t.records.size()) cudaEventRecord(t.records[slot_].stop, stream_);
+}
+
+}  // namespace evp
+
+using namespace evp;
+
+extern "C" {
+
+const char* evp_status_string(int32_t status) {
+    switch (status) {
+        case EVP_OK: return "EVP_OK";
+        case EVP_ERR_INVALID: return "EVP_ERR_INVALID: invalid argument";
+        case EVP_ERR_NONFINITE: return "EVP_ERR_NONFINITE: NaN or infinity in a float input";
+        case EVP_ERR_NO_MEMORY: return "EVP_ERR_NO_MEMORY: workspace too small or allocation refused";
+        case EVP_ERR_TIMEOUT: return "EVP_ERR_TIMEOUT: a bounded device wait gave up";
+        case EVP_ERR_CUDA: return "EVP_ERR_CUDA: a CUDA runtime call failed";
+        case EVP_ERR_UNSUPPORTED: return "EVP_ERR_UNSUPPORTED: outside this build's limits";
+        case EVP_ERR_RANGE: return "EVP_ERR_RANGE: index outside its array";
+        default: return "EVP_ERR_UNKNOWN";
+    }
+}
+
+int32_t evp_version(void) { return 100; }
+
+int32_t evp_words(int32_t d) { return d < 1 ? 0 : (d + 63) / 64; }
+
+int32_t evp_default_x(int32_t d) { return d < 1 ? 0 : (2 * d + 1) / 3; }
+
+int32_t evp_encode(const float* U, int64_t n, int32_t d, int32_t x, uint64_t* T,
+                   int32_t* dev_status, void* stream) {
+    if (n < 0 || d < 1 || x < 1 || x > d) return EVP_ERR_INVALID;
+    if (d > EVP_MAX_D_ENCODE) return EVP_ERR_UNSUPPORTED;
+    if (n == 0) return EVP_OK;
+    if (!U || !T) return EVP_ERR_INVALID;
+    cudaError_t e = launch_encode(U, n, d, x, T, dev_status, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+size_t ternary_knn_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k) {
+    if (nq <= 0 || ns <= 0 || d < 1 || k < 1) return 0;
+    return plan_popc_scan(nq, ns, d, k).ws_bytes;
+}
+
+int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int32_t d,
+                    int32_t x, int32_t k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
+                    int32_t* dev_status, void* stream) {
+    if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
+        (int64_t)k > ns)
+        return EVP_ERR_INVALID;
+    if (d > EVP_MAX_D_SCAN || k > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
+    if (nq == 0) return EVP_OK;
+    if (!Q || !S || !ids || !dist || !ws) return EVP_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(S) & 15) != 0 || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
+        return EVP_ERR_INVALID;
+    return run_popc_knn(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d,
+               const int64_t* shortlist, int32_t n, int32_t k, int64_t* ids, float* scores,
+               int32_t* dev_status, void* stream) {
+    if (nq < 0 || ns < 1 || d < 1 || n < 1 || k < 1 || k > n) return EVP_ERR_INVALID;
+    if (d > EVP_MAX_D_RERANK || n > EVP_MAX_SHORTLIST) return EVP_ERR_UNSUPPORTED;
+    if (nq == 0) return EVP_OK;
+    if (!Q || !S || !shortlist || !ids || !scores) return EVP_ERR_INVALID;
+    cudaError_t e = launch_rerank(Q, nq, S, ns, d, shortlist, n, k, ids, scores, dev_status,
+                                  static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+int32_t evp_timing_enable(int32_t on) {
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> g(t.mu);
+    t.enabled = on != 0;
+    return EVP_OK;
+}
+
+int32_t evp_timing_reset(void) {
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> g(t.mu);
+    for (auto& r : t.records) {
+        cudaEventSynchronize(r.stop);
+        t.spare.push_back(r.start);
+        t.spare.push_back(r.stop);
+    }
+    t.records.clear();
+    return EVP_OK;
+}
+
+int32_t evp_timing_read(const char* name, int64_t* launches, double* total_ms) {
+    if (!name || !launches || !total_ms) return EVP_ERR_INVALID;
+    TimingState& t = timing();
+    std::lock_guard<std::mutex> g(t.mu);
+    int64_t n = 0;
+    double ms = 0.0;
+    for (auto& r : t.records) {
+        if (std::strcmp(r.name, name) != 0) continue;
+        if (cudaEventSynchronize(r.stop) != cudaSuccess) return EVP_ERR_CUDA;
+        float f = 0.f;
+        if (cudaEventElapsedTime(&f, r.start, r.stop) != cudaSuccess) return EVP_ERR_CUDA;
+        ms += f;
+        ++n;
+    }
+    *launches = n;
+    *total_ms = ms;
+    return EVP_OK;
+}
+
+}  // extern "C"

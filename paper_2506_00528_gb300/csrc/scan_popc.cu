@@ -1,0 +1,428 @@
+// ternary_knn, popcount path: exhaustive scan of packed ternary codes with
+// the integer proxy distance Delta and a fused per-query top-k.
+//
+// Delta(q, s) = ||q - s||^2 over ternary vectors (read of the notation
+// table and Sec. 2.6).  With m = v+ | v- (non-zero mask) and sigma = v-
+// (sign), per 64-bit word:
+//   one_nz  = q.m ^ s.m                 -> elements where exactly one is 0: (v-w)^2 = 1
+//   opposed = q.m & s.m & (q.sig ^ s.sig) -> both non-zero, opposite sign:   (v-w)^2 = 4
+//   Delta   = sum popc(one_nz) + 4 * sum popc(opposed)
+// which equals 2x - 2*b2sp for two codes with x non-zeros each, b2sp being
+// the four-term bitplane scalar product of Sec. 5.1.2.
+//
+// Kernel layout (one CTA per SM, persistent over a contiguous slice of the
+// database; 256 threads, one database row per thread per tile):
+//   * database tiles of 256 rows are staged into shared memory by TMA
+//     (cp.async.bulk.tensor.2d) through a ring of mbarrier-tracked stages.
+//     The box is wider than a row (2(W+p) words, p chosen so the row
+//     pitch in 16-byte units is odd); the extra words are filled with 0 by
+//     the TMA unit and make the per-thread row reads bank-conflict free;
+//   * the pass's queries (up to 16) sit in shared memory as (m, sigma)
+//     word pairs and are read by broadcast;
+//   * a row whose key (Delta << 32 | row) beats the query's threshold tau
+//     is appended to that query's candidate buffer; buffers are merged
+//     (bitonic sort + merge-path) into a per-(query, slice) sorted list of
+//     the k best, kept in the workspace;
+//   * once a slice's list is full, its k-th key is folded into a global
+//     per-query threshold with atomicMin, and every CTA filters with the
+//     smaller of its own and the global threshold.  Any key above the
+//     global threshold has k better keys in some slice, so it cannot be in
+//     the answer.
+// A second kernel merges, per query, the slice lists' keys that do not
+// exceed the final global threshold into the k best.
+#include "evp_internal.cuh"
+
+#include <algorithm>
+
+namespace evp {
+
+namespace {
+
+constexpr int SCAN_ROWS = 256;                  // rows per tile = threads per CTA
+constexpr int CAND_CAP = 512;                   // candidate slots per query (power of 2)
+constexpr int MERGE_AT = CAND_CAP - SCAN_ROWS;  // merge before a tile could overflow
+constexpr int QB_MAX = 16;
+constexpr int MAX_STAGES = 4;
+constexpr int SMEM_BUDGET = 225 * 1024;
+constexpr int FM_WARPS = 4;                     // final merge: queries per CTA
+
+struct ScanArgs {
+    const uint64_t* Q;  // this pass's query codes [nqg][2W]
+    int nqg;
+    int64_t ns;
+    int W;
+    int k;
+    int pitch;           // uint64 words per staged row
+    int stages;
+    int64_t tiles_per_slice;
+    int64_t ntiles;
+    uint64_t* lists;     // [QB_MAX][nslices][2][k]
+    int32_t* meta;       // [QB_MAX][nslices][2]: (length, current buffer)
+    uint64_t* tau_global;  // [QB_MAX]
+    int32_t* status;
+};
+
+__host__ __device__ inline int row_pitch_words(int W) { return 2 * (W + ((W & 1) ? 2 : 1)); }
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct SmemLayout {
+    size_t stage_bytes, qv_off, cand_off, tau_off, cnt_off, bar_off, flag_off, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int W, int stages) {
+    SmemLayout L;
+    L.stage_bytes = align_up((size_t)SCAN_ROWS * row_pitch_words(W) * 8, 1024);
+    L.qv_off = L.stage_bytes * stages;
+    L.cand_off = L.qv_off + align_up((size_t)QB_MAX * W * 16, 128);
+    L.tau_off = L.cand_off + (size_t)QB_MAX * CAND_CAP * 8;
+    L.cnt_off = L.tau_off + QB_MAX * 8;
+    L.bar_off = L.cnt_off + align_up(3 * QB_MAX * 4, 8);
+    L.flag_off = L.bar_off + MAX_STAGES * 8;
+    L.total = L.flag_off + 16;
+    return L;
+}
+
+__device__ inline int next_pow2(int v) {
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+template <int QB>
+__global__ void __launch_bounds__(SCAN_ROWS, 1)
+scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const SmemLayout L = smem_layout(a.W, a.stages);
+    uint64_t* qv = reinterpret_cast<uint64_t*>(smem + L.qv_off);
+    uint64_t* cand = reinterpret_cast<uint64_t*>(smem + L.cand_off);
+    uint64_t* tau = reinterpret_cast<uint64_t*>(smem + L.tau_off);
+    int* cnt = reinterpret_cast<int*>(smem + L.cnt_off);
+    int* len = cnt + QB_MAX;
+    int* cur = len + QB_MAX;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    int* abort_flag = reinterpret_cast<int*>(smem + L.flag_off);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int W = a.W, k = a.k, nslices = gridDim.x, slice = blockIdx.x;
+    const int64_t tile0 = (int64_t)slice * a.tiles_per_slice;
+    const int64_t tile_end = min(tile0 + a.tiles_per_slice, a.ntiles);
+    const int ntl = tile_end > tile0 ? (int)(tile_end - tile0) : 0;
+    const uint32_t tile_bytes = (uint32_t)(SCAN_ROWS * a.pitch * 8);
+
+    if (tid == 0) {
+        for (int s = 0; s < a.stages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        *abort_flag = 0;
+    }
+    for (int i = tid; i < QB * W; i += SCAN_ROWS) {
+        const int q = i / W, w = i - q * W;
+        uint64_t p = 0, n = 0;
+        if (q < a.nqg) {
+            p = a.Q[(int64_t)q * 2 * W + w];
+            n = a.Q[(int64_t)q * 2 * W + W + w];
+        }
+        qv[2 * i] = p | n;
+        qv[2 * i + 1] = n;
+    }
+    if (tid < QB) {
+        tau[tid] = KEY_NONE;
+        cnt[tid] = 0;
+        len[tid] = 0;
+        cur[tid] = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int pre = min(a.stages, ntl);
+        for (int s = 0; s < pre; ++s) {
+            mbar_arrive_expect_tx(&bars[s], tile_bytes);
+            tma_load_2d(smem + s * L.stage_bytes, &tmap, &bars[s], 0,
+                        (int32_t)((tile0 + s) * SCAN_ROWS));
+        }
+    }
+
+    int it = 0;
+    for (; it < ntl; ++it) {
+        const int s = it % a.stages;
+        const uint32_t parity = (uint32_t)((it / a.stages) & 1);
+        if (tid == 0 && !mbar_wait_bounded(&bars[s], parity)) {
+            report(a.status, EVP_ERR_TIMEOUT);
+            *abort_flag = 1;
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+
+        const int64_t row = (tile0 + it) * SCAN_ROWS + tid;
+        if (row < a.ns) {
+            const uint64_t* rp =
+                reinterpret_cast<const uint64_t*>(smem + s * L.stage_bytes) + tid * a.pitch;
+            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qv);
+            int acc_one[QB], acc_opp[QB];
+#pragma unroll
+            for (int q = 0; q < QB; ++q) acc_one[q] = acc_opp[q] = 0;
+#pragma unroll 2
+            for (int w = 0; w < W; ++w) {
+                const uint64_t sp = rp[w], sn = rp[W + w];
+                const uint64_t sm = sp | sn;
+#pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    const ulonglong2 qq = q2[q * W + w];
+                    acc_one[q] += __popcll(qq.x ^ sm);
+                    acc_opp[q] += __popcll(qq.x & sm & (qq.y ^ sn));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < QB; ++q) {
+                if (q < a.nqg) {
+                    const uint32_t delta = (uint32_t)(acc_one[q] + 4 * acc_opp[q]);
+                    const uint64_t key = ((uint64_t)delta << 32) | (uint64_t)row;
+                    if (key < tau[q]) {
+                        const int pos = atomicAdd(&cnt[q], 1);
+                        cand[q * CAND_CAP + pos] = key;
+                    }
+                }
+            }
+        }
+        __syncthreads();  // stage s consumed, candidates visible
+        if (tid == 0 && it + a.stages < ntl) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[s], tile_bytes);
+            tma_load_2d(smem + s * L.stage_bytes, &tmap, &bars[s], 0,
+                        (int32_t)((tile0 + it + a.stages) * SCAN_ROWS));
+        }
+        const bool last = it == ntl - 1;
+        uint32_t mask = 0;
+#pragma unroll
+        for (int q = 0; q < QB; ++q) {
+            const int c = cnt[q];
+            if (c > MERGE_AT || (last && c > 0)) mask |= 1u << q;
+        }
+        if (mask) {
+            __syncthreads();  // every thread has read cnt before it changes
+            for (int q = warp; q < QB; q += SCAN_ROWS / 32) {
+                if (!((mask >> q) & 1)) continue;
+                uint64_t* C = cand + q * CAND_CAP;
+                const int nc = cnt[q];
+                const int P = next_pow2(nc);
+                for (int i = nc + lane; i < P; i += 32) C[i] = KEY_NONE;
+                __syncwarp();
+                warp_bitonic_sort(C, P);
+                uint64_t* base = a.lists + ((int64_t)q * nslices + slice) * 2 * k;
+                const int c0 = cur[q];
+                const int nl = warp_merge_topk(base + c0 * k, len[q], C, nc, base + (c0 ^ 1) * k, k);
+                if (lane == 0) {
+                    cur[q] = c0 ^ 1;
+                    len[q] = nl;
+                    cnt[q] = 0;
+                    uint64_t t = tau[q];
+                    if (nl == k) {
+                        const uint64_t kth = base[(c0 ^ 1) * k + k - 1];
+                        const unsigned long long old =
+                            atomicMin(reinterpret_cast<unsigned long long*>(&a.tau_global[q]),
+                                      (unsigned long long)kth);
+                        t = min(t, min(kth, (uint64_t)old));
+                    } else {
+                        t = min(t, *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
+                    }
+                    tau[q] = t;
+                }
+            }
+            __syncthreads();
+        } else if (tid < QB) {
+            tau[tid] = min(tau[tid], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[tid]));
+        }
+    }
+
+    if (*abort_flag) {
+        // drain the loads still in flight before the CTA exits
+        if (tid == 0) {
+            const int issued = min(ntl, it + a.stages);
+            for (int j = it + 1; j < issued; ++j)
+                if (!mbar_wait_bounded(&bars[j % a.stages], (uint32_t)((j / a.stages) & 1))) break;
+        }
+        return;
+    }
+    if (tid < QB) {
+        int32_t* m = a.meta + ((int64_t)tid * nslices + slice) * 2;
+        m[0] = len[tid];
+        m[1] = cur[tid];
+    }
+}
+
+__global__ void init_tau_kernel(uint64_t* tau_global) {
+    if (threadIdx.x < QB_MAX) tau_global[threadIdx.x] = KEY_NONE;
+}
+
+// Per query (one warp): the keys of all slice lists that do not exceed the
+// final global threshold, merged into the k best.
+__global__ void __launch_bounds__(FM_WARPS * 32)
+final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
+                   const uint64_t* __restrict__ tau_global, int nqg, int nslices, int k,
+                   int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = blockIdx.x * FM_WARPS + warp;
+    if (q >= nqg) return;
+    uint64_t* C = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * (CAND_CAP + 2 * k);
+    uint64_t* Lb = C + CAND_CAP;
+    const uint64_t tau_f = tau_global[q];
+    const unsigned lt = (1u << lane) - 1u;
+    int nl = 0, c = 0, nc = 0;
+
+    auto flush = [&]() {
+        const int P = next_pow2(nc);
+        for (int i = nc + lane; i < P; i += 32) C[i] = KEY_NONE;
+        __syncwarp();
+        warp_bitonic_sort(C, P);
+        nl = warp_merge_topk(Lb + c * k, nl, C, nc, Lb + (c ^ 1) * k, k);
+        c ^= 1;
+        nc = 0;
+        __syncwarp();
+    };
+
+    for (int s = 0; s < nslices; ++s) {
+        const int32_t* m = meta + ((int64_t)q * nslices + s) * 2;
+        const int ln = m[0];
+        const uint64_t* src = lists + (((int64_t)q * nslices + s) * 2 + m[1]) * k;
+        for (int b = 0; b < ln; b += 32) {
+            const int i = b + lane;
+            const uint64_t key = i < ln ? src[i] : KEY_NONE;
+            const bool ok = key != KEY_NONE && key <= tau_f;
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) C[nc + __popc(bal & lt)] = key;
+            nc += __popc(bal);
+            if (nc > CAND_CAP - 32) flush();
+        }
+    }
+    if (nc > 0) flush();
+    for (int j = lane; j < k; j += 32) {
+        const uint64_t key = j < nl ? Lb[c * k + j] : KEY_NONE;
+        ids[(int64_t)q * k + j] = key == KEY_NONE ? -1 : (int64_t)(key & 0xffffffffull);
+        dist[(int64_t)q * k + j] = key == KEY_NONE ? -1 : (int32_t)(key >> 32);
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+int choose_stages(int W) {
+    for (int st = MAX_STAGES; st >= 2; --st)
+        if (smem_layout(W, st).total <= (size_t)SMEM_BUDGET) return st;
+    return 0;
+}
+
+template <int QB>
+cudaError_t launch_scan(const CUtensorMap& tmap, const ScanArgs& a, int nslices, size_t smem,
+                        cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<QB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BUDGET + 2048);
+    if (e != cudaSuccess) return e;
+    TimedLaunch timer("scan_popc", stream);
+    scan_popc_kernel<QB><<<nslices, SCAN_ROWS, smem, stream>>>(tmap, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k) {
+    ScanPlan p{};
+    const int64_t ntiles = std::max<int64_t>(1, (ns + SCAN_ROWS - 1) / SCAN_ROWS);
+    const int64_t tps = (ntiles + num_sms() - 1) / num_sms();  // tiles per slice
+    p.nslices = (int)((ntiles + tps - 1) / tps);
+    p.qb = (int)std::min<int64_t>(QB_MAX, std::max<int64_t>(1, nq));
+    p.groups = (int)((nq + QB_MAX - 1) / QB_MAX);
+    p.list_bytes = align_up((size_t)QB_MAX * p.nslices * 2 * k * 8, 256);
+    const size_t meta_bytes = align_up((size_t)QB_MAX * p.nslices * 2 * 4, 256);
+    p.ws_bytes = p.list_bytes + meta_bytes + 256;
+    (void)d;
+    return p;
+}
+
+int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
+                     int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
+                     int32_t* status, cudaStream_t stream) {
+    (void)x;
+    const int W = (d + 63) / 64;
+    const ScanPlan p = plan_popc_scan(nq, ns, d, k);
+    if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
+    const int stages = choose_stages(W);
+    if (stages == 0) return EVP_ERR_UNSUPPORTED;
+    const SmemLayout L = smem_layout(W, stages);
+
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return EVP_ERR_CUDA;
+    CUtensorMap tmap;
+    const int pitch = row_pitch_words(W);
+    cuuint64_t gdim[2] = {(cuuint64_t)(2 * W), (cuuint64_t)ns};
+    cuuint64_t gstride[1] = {(cuuint64_t)(16 * W)};
+    cuuint32_t box[2] = {(cuuint32_t)pitch, (cuuint32_t)SCAN_ROWS};
+    cuuint32_t estride[2] = {1, 1};
+    CUresult cr = enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(S), gdim,
+                      gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                      CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return EVP_ERR_CUDA;
+
+    uint8_t* wsb = static_cast<uint8_t*>(ws);
+    ScanArgs a{};
+    a.ns = ns;
+    a.W = W;
+    a.k = k;
+    a.pitch = pitch;
+    a.stages = stages;
+    a.ntiles = (ns + SCAN_ROWS - 1) / SCAN_ROWS;
+    a.tiles_per_slice = (a.ntiles + num_sms() - 1) / num_sms();
+    a.lists = reinterpret_cast<uint64_t*>(wsb);
+    a.meta = reinterpret_cast<int32_t*>(wsb + p.list_bytes);
+    a.tau_global = reinterpret_cast<uint64_t*>(wsb + p.ws_bytes - 256);
+    a.status = status;
+
+    const size_t fm_smem = (size_t)FM_WARPS * (CAND_CAP + 2 * k) * 8;
+    if (cudaFuncSetAttribute(final_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FM_WARPS * (CAND_CAP + 2 * EVP_MAX_K) * 8) != cudaSuccess)
+        return EVP_ERR_CUDA;
+
+    for (int g = 0; g < p.groups; ++g) {
+        const int64_t q0 = (int64_t)g * QB_MAX;
+        const int nqg = (int)std::min<int64_t>(QB_MAX, nq - q0);
+        a.Q = Q + q0 * 2 * W;
+        a.nqg = nqg;
+        {
+            TimedLaunch timer("scan_init", stream);
+            init_tau_kernel<<<1, 32, 0, stream>>>(a.tau_global);
+        }
+        cudaError_t e;
+        if (nqg <= 1) e = launch_scan<1>(tmap, a, p.nslices, L.total, stream);
+        else if (nqg <= 2) e = launch_scan<2>(tmap, a, p.nslices, L.total, stream);
+        else if (nqg <= 4) e = launch_scan<4>(tmap, a, p.nslices, L.total, stream);
+        else if (nqg <= 8) e = launch_scan<8>(tmap, a, p.nslices, L.total, stream);
+        else e = launch_scan<16>(tmap, a, p.nslices, L.total, stream);
+        if (e != cudaSuccess) return EVP_ERR_CUDA;
+        {
+            TimedLaunch timer("final_merge", stream);
+            final_merge_kernel<<<(nqg + FM_WARPS - 1) / FM_WARPS, FM_WARPS * 32, fm_smem,
+                                 stream>>>(a.lists, a.meta, a.tau_global, nqg, p.nslices, k,
+                                           ids + q0 * k, dist + q0 * k);
+        }
+        if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
+    }
+    return EVP_OK;
+}
+
+}  // namespace evp

@@ -36,3 +36,20 @@ def read_golden_rows(name):
             if line:
                 rows.append(line.split())
     return rows
+
+
+@pytest.fixture(scope="session")
+def evp_lib():
+    """Build (if stale) and load libevp; GPU tests only."""
+    from paper_2506_00528_gb300 import build as b
+    b.build()
+    from paper_2506_00528_gb300 import evp
+    evp.load()
+    return evp
+
+
+@pytest.fixture(scope="session")
+def dev():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch.device("cuda:0")

@@ -1,0 +1,98 @@
+"""CPU checks of the C-ABI library: it builds, loads without a GPU, exports
+every symbol the public headers declare, and its host-only helpers agree
+with the oracle.  No compute call is made here (there is no GPU)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+import oracle
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2506_00528_gb300 import build as b
+    path = b.build()
+    return ctypes.CDLL(path)
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(([^;{}]*)\)\s*;", text):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "sizeof", "return"):
+                names.add(name)
+    return sorted(names)
+
+
+def test_header_declares_the_boundary_calls():
+    names = _declared_functions()
+    for required in ("evp_encode", "ternary_knn", "ternary_knn_workspace", "rerank",
+                     "evp_words", "evp_default_x", "evp_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header():
+    from paper_2506_00528_gb300 import evp
+    assert set(_declared_functions()) <= set(evp.SIGNATURES), \
+        set(_declared_functions()) - set(evp.SIGNATURES)
+
+
+def test_host_helpers_match_oracle(lib):
+    lib.evp_default_x.restype = ctypes.c_int32
+    lib.evp_words.restype = ctypes.c_int32
+    for d in list(range(1, 3001)) + [4096, 8191, 100000]:
+        assert lib.evp_default_x(d) == oracle.default_x(d), d
+        assert lib.evp_words(d) == oracle.words(d)
+    assert lib.evp_default_x(0) == 0 and lib.evp_words(0) == 0
+
+
+def test_status_strings(lib):
+    lib.evp_status_string.restype = ctypes.c_char_p
+    for code in range(8):
+        s = lib.evp_status_string(code).decode()
+        assert s.startswith("EVP_")
+    assert b"UNKNOWN" in lib.evp_status_string(99)
+
+
+def test_argument_errors_detected_on_host(lib):
+    """Invalid arguments are rejected before any CUDA call (works without a GPU)."""
+    lib.evp_encode.restype = ctypes.c_int32
+    P = ctypes.c_void_p
+    fake = P(0x1000)
+    i64, i32 = ctypes.c_int64, ctypes.c_int32
+    # x > d, x < 1, d < 1
+    assert lib.evp_encode(fake, i64(4), i32(8), i32(9), fake, None, None) == 1
+    assert lib.evp_encode(fake, i64(4), i32(8), i32(0), fake, None, None) == 1
+    assert lib.evp_encode(fake, i64(4), i32(0), i32(1), fake, None, None) == 1
+    # d above the encode limit
+    assert lib.evp_encode(fake, i64(4), i32(4096), i32(5), fake, None, None) == 6
+    # n == 0 is a no-op
+    assert lib.evp_encode(None, i64(0), i32(8), i32(3), None, None, None) == 0
+    lib.ternary_knn.restype = ctypes.c_int32
+    sz = ctypes.c_size_t
+    # k > ns
+    assert lib.ternary_knn(fake, i64(1), fake, i64(5), i32(8), i32(3), i32(6), fake, fake,
+                           fake, sz(1 << 20), None, None) == 1
+    # d above the scan limit
+    assert lib.ternary_knn(fake, i64(1), fake, i64(5), i32(2000), i32(3), i32(2), fake, fake,
+                           fake, sz(1 << 20), None, None) == 6
+    # misaligned database pointer
+    assert lib.ternary_knn(fake, i64(1), P(0x1008), i64(5), i32(8), i32(3), i32(2), fake, fake,
+                           fake, sz(1 << 20), None, None) == 1
+    lib.rerank.restype = ctypes.c_int32
+    # k > n
+    assert lib.rerank(fake, i64(1), fake, i64(5), i32(8), fake, i32(3), i32(4), fake, fake,
+                      None, None) == 1

@@ -1,0 +1,82 @@
+"""Parity at the full workload sizes.
+
+* 1,000,000 x 768 Gaussian mixture (1,024 centres, anisotropic scales),
+  x in {64, 256, 384}, k = 100: the oracle encodes the whole database and
+  checks several queries exhaustively (bit-exact ids and Delta).
+* 10,000,000 x 768, x = 512, 1,024 queries, shortlist 100 then rerank to
+  10 -- the benchmark's launch configuration -- checked on sampled queries
+  through properties the oracle computes row by row.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2506_00528_gb300 import synth
+from oracle_par import check_knn_sampled, encode as par_encode, knn as par_knn
+from test_gpu_rerank import check_rerank
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def db_1m(dev):
+    U = synth.mixture_torch(1_000_000, 768, n_centres=1024, anisotropic=True,
+                            stream=synth.STREAM_DB, device=dev)
+    Q = synth.mixture_torch(40, 768, n_centres=1024, anisotropic=True,
+                            stream=synth.STREAM_QUERIES, device=dev)
+    return U, Q, U.cpu().numpy(), Q.cpu().numpy()
+
+
+@pytest.mark.parametrize("x", [64, 256, 384])
+def test_scale_1m_exhaustive_queries(evp_lib, dev, db_1m, x):
+    U, Q, U_h, Q_h = db_1m
+    d, k = 768, 100
+    st = evp_lib.new_status(dev)
+    Ts = evp_lib.encode(U, x, status=st)
+    Tq = evp_lib.encode(Q, x, status=st)
+    ids, dist = evp_lib.ternary_knn(Tq, Ts, d, x, k, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    Vs = par_encode(U_h, x)
+    Vq = oracle.encode(Q_h, x)
+    # encode: bit-exact on the full database
+    np.testing.assert_array_equal(Ts.cpu().numpy().view(np.uint64), oracle.pack(Vs))
+    sel = [0, 15, 16, 39]   # first pass, its last query, second pass, last pass
+    oi, od = par_knn(Vq[sel], Vs, k)
+    np.testing.assert_array_equal(ids.cpu().numpy()[sel], oi)
+    np.testing.assert_array_equal(dist.cpu().numpy()[sel], od)
+
+
+def test_bench_workload_10m_sampled(evp_lib, dev):
+    n, d, x, nq, n_sl, k = 10_000_000, 768, 512, 1024, 100, 10
+    U = synth.mixture_torch(n, d, n_centres=1024, anisotropic=True, stream=synth.STREAM_DB,
+                            device=dev)
+    Q = synth.mixture_torch(nq, d, n_centres=1024, anisotropic=True,
+                            stream=synth.STREAM_QUERIES, device=dev)
+    st = evp_lib.new_status(dev)
+    Ts = evp_lib.encode(U, x, status=st)
+    Tq = evp_lib.encode(Q, x, status=st)
+    sl, sd = evp_lib.ternary_knn(Tq, Ts, d, x, n_sl, status=st)
+    rid, rsc = evp_lib.rerank(Q, U, sl, k, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rng = np.random.default_rng(123)
+    sample_idx = np.sort(rng.choice(n, 50_000, replace=False))
+    U_sample = U[torch.from_numpy(sample_idx).to(dev)].cpu().numpy()
+    V_sample = par_encode(U_sample, x)
+    # encode bit-exact on the sampled rows
+    np.testing.assert_array_equal(Ts[torch.from_numpy(sample_idx).to(dev)].cpu().numpy()
+                                  .view(np.uint64), oracle.pack(V_sample))
+    Q_h = Q.cpu().numpy()
+    Vq = oracle.encode(Q_h, x)
+    sl_h, sd_h = sl.cpu().numpy(), sd.cpu().numpy()
+    for q in (0, 17, 511, 1023):
+        rows = U[torch.from_numpy(sl_h[q]).to(dev)].cpu().numpy()
+        check_knn_sampled(Vq[q], sl_h[q], sd_h[q], oracle.encode(rows, x), V_sample, sample_idx)
+        # rerank of that query's shortlist against float64
+        S_rows = rows
+        local = np.arange(n_sl, dtype=np.int64)[None, :]
+        gi = rid.cpu().numpy()[q:q + 1]
+        g_local = np.array([[int(np.where(sl_h[q] == i)[0][0]) for i in gi[0]]])
+        check_rerank(g_local, rsc.cpu().numpy()[q:q + 1], Q_h[q:q + 1], S_rows, local, k)
