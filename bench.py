@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--centres", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 popcount, 2 tensor core")
     return ap.parse_args()
 
 
@@ -230,18 +231,26 @@ def main():
     Qall = synth.mixture_torch(pool * B, d, n_centres=a.centres, anisotropic=True,
                                stream=synth.STREAM_QUERIES + 10 * rank, device=dev)
     Qb = [Qall[i * B:(i + 1) * B] for i in range(pool)]
+    db = evp.Database(S, U, d, x, tensor_copy=(a.path != 1))
     Tq = torch.empty((B, 2 * W), dtype=torch.int64, device=dev)
     sl = torch.empty((B, n_sl), dtype=torch.int64, device=dev)
     sd = torch.empty((B, n_sl), dtype=torch.int32, device=dev)
-    ws = torch.empty(evp.knn_workspace_bytes(B, n, d, n_sl), dtype=torch.uint8, device=dev)
     rid = torch.empty((B, k), dtype=torch.int64, device=dev)
     rsc = torch.empty((B, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    if a.path == 0:
+        ws = torch.empty(db.search_workspace_bytes(B, n_sl, k), dtype=torch.uint8, device=dev)
+    else:
+        ws = torch.empty(int(evp.load().evp_db_knn_workspace(db.handle, B, n_sl, a.path)),
+                         dtype=torch.uint8, device=dev)
 
     def step(Q):
-        evp.encode(Q, x, out=Tq, status=st, stream=stream)
-        evp.ternary_knn(Tq, S, d, x, n_sl, ids=sl, dist=sd, ws=ws, status=st, stream=stream)
-        evp.rerank(Q, U, sl, k, ids=rid, scores=rsc, status=st, stream=stream)
+        if a.path == 0:   # one C-ABI call: encode -> scan -> rerank
+            db.search(Q, n_sl, k, ids=rid, scores=rsc, ws=ws, status=st, stream=stream)
+        else:             # the same three steps with the scan path forced
+            evp.encode(Q, x, out=Tq, status=st, stream=stream)
+            db.knn(Tq, n_sl, ids=sl, dist=sd, ws=ws, status=st, stream=stream, path=a.path)
+            evp.rerank(Q, U, sl, k, ids=rid, scores=rsc, status=st, stream=stream)
 
     for i in range(a.warmup):
         step(Qb[i % pool])
@@ -270,7 +279,8 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     per_kernel = {name: evp.timing_read(name) for name in
-                  ("encode", "scan_init", "scan_popc", "final_merge", "rerank")}
+                  ("encode", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
+                               "final_merge", "rerank")}
     evp.check_status(st, "timed steps")
     if world > 1:
         t = torch.tensor([ms], device=dev)
@@ -281,23 +291,28 @@ def main():
 
     # ---- end to end through the API with host buffers (pinned)
     Qh = [q.cpu().pin_memory() for q in Qb]
-    Qd = torch.empty((B, d), dtype=torch.float32, device=dev)
     ids_h = torch.empty((B, k), dtype=torch.int64).pin_memory()
     sc_h = torch.empty((B, k), dtype=torch.float32).pin_memory()
+    ws_h = torch.empty(db.search_host_workspace_bytes(B, n_sl, k), dtype=torch.uint8, device=dev)
+    Qd = torch.empty((B, d), dtype=torch.float32, device=dev)
+
+    def step_host(i):
+        if a.path == 0:   # evp_db_search_host: H2D, encode, scan, rerank, D2H
+            db.search_host(Qh[i % pool], n_sl, k, ids_h, sc_h, ws=ws_h, status=st, stream=stream)
+        else:
+            Qd.copy_(Qh[i % pool], non_blocking=True)
+            step(Qd)
+            ids_h.copy_(rid, non_blocking=True)
+            sc_h.copy_(rsc, non_blocking=True)
+
     for i in range(a.warmup):
-        Qd.copy_(Qh[i % pool], non_blocking=True)
-        step(Qd)
-        ids_h.copy_(rid, non_blocking=True)
-        sc_h.copy_(rsc, non_blocking=True)
+        step_host(i)
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     e0.record(stream)
     for i in range(a.steps):
-        Qd.copy_(Qh[i % pool], non_blocking=True)
-        step(Qd)
-        ids_h.copy_(rid, non_blocking=True)
-        sc_h.copy_(rsc, non_blocking=True)
+        step_host(i)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -307,31 +322,48 @@ def main():
         e2e_ms = float(t.item())
     e2e_value = world * B * a.steps / (e2e_ms / 1000.0)
 
-    # ---- roofline of the dominant kernel (the popcount scan)
+    # ---- roofline of the dominant kernel
     hbm_peak, bf16_peak, peak_src = load_peaks()
-    n_scan, scan_ms = per_kernel["scan_popc"]
-    scan_avg_ms = scan_ms / max(1, n_scan)
-    # algorithmic work per scan launch: one pass over the database codes for
-    # up to 16 queries; per (query, row) pair 4W 32-bit popcounts.
-    passes_per_step = (B + 15) // 16
-    pairs_per_launch = n * (B / passes_per_step)
-    popc_per_launch = pairs_per_launch * 4 * W
-    bytes_per_launch = n * 16 * W
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    popc_peak = POPC_PER_CLK_PER_SM * sm_count * 2070e6
-    roofline = {
-        "kernel": "scan_popc",
-        "bound": "alu",
-        "achieved": popc_per_launch / (scan_avg_ms / 1e3) / 1e12,
-        "peak": popc_peak / 1e12,
-        "unit": "Tpopc/s",
-        "frac": (popc_per_launch / (scan_avg_ms / 1e3)) / popc_peak,
-        "traffic": None,
-        "hbm_achieved_gbs": bytes_per_launch / (scan_avg_ms / 1e3) / 1e9,
-        "hbm_peak_gbs": hbm_peak,
-        "peak_source": f"POPC 16/clk/SM (probe) x {sm_count} SMs x 2070 MHz; HBM {peak_src}",
-        "launches": n_scan, "avg_ms": scan_avg_ms,
-    }
+    n_mma, mma_ms = per_kernel["scan_mma"]
+    n_scan, scan_ms = per_kernel["scan_popc"]
+    if mma_ms >= scan_ms:
+        # tensor-core scan: algorithmic flops = 2 d per (query, row) pair
+        avg = mma_ms / max(1, n_mma)
+        flops = 2.0 * d * B * n * (a.steps / max(1, n_mma))
+        fp8_peak = 2.0 * bf16_peak   # nominal fp8 : bf16 dense ratio 2 : 1
+        roofline = {
+            "kernel": "scan_mma", "bound": "tensor",
+            "achieved": flops / (avg / 1e3) / 1e12, "peak": fp8_peak, "unit": "TFLOP/s",
+            "frac": flops / (avg / 1e3) / 1e12 / fp8_peak, "traffic": None,
+            "peak_source": f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s ({peak_src})",
+            "launches": n_mma, "avg_ms": avg,
+        }
+    else:
+        # popcount scan: one pass over the codes per <= 16 queries; per
+        # (query, row) pair 4W 32-bit popcounts
+        avg = scan_ms / max(1, n_scan)
+        passes_per_step = (B + 15) // 16
+        pairs_per_launch = n * (B / passes_per_step)
+        popc_per_launch = pairs_per_launch * 4 * W
+        bytes_per_launch = n * 16 * W
+        popc_peak = POPC_PER_CLK_PER_SM * sm_count * 2070e6
+        hbm_bound = B <= 3
+        roofline = {
+            "kernel": "scan_popc",
+            "bound": "hbm" if hbm_bound else "alu",
+            "achieved": (bytes_per_launch / (avg / 1e3) / 1e9) if hbm_bound
+            else popc_per_launch / (avg / 1e3) / 1e12,
+            "peak": hbm_peak if hbm_bound else popc_peak / 1e12,
+            "unit": "GB/s" if hbm_bound else "Tpopc/s",
+            "frac": (bytes_per_launch / (avg / 1e3) / 1e9 / hbm_peak) if hbm_bound
+            else (popc_per_launch / (avg / 1e3)) / popc_peak,
+            "traffic": None,
+            "hbm_achieved_gbs": bytes_per_launch / (avg / 1e3) / 1e9,
+            "popc_achieved_tops": popc_per_launch / (avg / 1e3) / 1e12,
+            "peak_source": f"POPC 16/clk/SM (probe) x {sm_count} SMs x 2070 MHz; HBM {peak_src}",
+            "launches": n_scan, "avg_ms": avg,
+        }
     kernels = {nm: {"launches": c, "total_ms": round(t, 3)} for nm, (c, t) in per_kernel.items()}
 
     # ---- recall@10 against exact float32 cosine kNN (first 64 queries)
@@ -353,7 +385,9 @@ def main():
             best_i = torch.gather(cat_i, 1, j)
         truth = best_i.cpu().numpy()
         got_rr = rid[:nrq].cpu().numpy()
-        got_tern = sl[:nrq, :k].cpu().numpy()
+        tq = evp.encode(Qr.contiguous(), x)
+        tern_ids, _ = db.knn(tq, k)
+        got_tern = tern_ids.cpu().numpy()
         recall = {
             "rerank_10_at_100": float(np.mean([len(set(a_) & set(b_)) / k
                                                for a_, b_ in zip(got_rr, truth)])),

@@ -139,6 +139,31 @@ int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns
                     int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist,
                     void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
 
+/* Scan paths.  Both return identical results.
+ *   EVP_PATH_POPC  bitplane popcount scan on the integer pipe: reads the
+ *                  packed codes once per 16 queries; best for small batches.
+ *   EVP_PATH_MMA   tensor-core scan (tcgen05, e4m3 operands holding -1/0/+1,
+ *                  float32 accumulation, exact): the codes are expanded to
+ *                  one byte per element (in the workspace when S is given
+ *                  packed); requires k <= 128.
+ *   EVP_PATH_AUTO  MMA when nq > 16 and k <= 128, POPC otherwise.  This is
+ *                  what ternary_knn uses.
+ * The MMA path assumes every code has exactly x non-zeros (as evp_encode
+ * produces): it computes Delta as 2x - 2*b2sp.  The POPC path computes
+ * ||q - s||^2 directly. */
+#define EVP_PATH_AUTO 0
+#define EVP_PATH_POPC 1
+#define EVP_PATH_MMA  2
+#define EVP_MMA_MAX_K 128
+
+size_t ternary_knn_path_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k,
+                                  int32_t path);
+
+int32_t ternary_knn_path(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns,
+                         int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist,
+                         void* ws, size_t ws_bytes, int32_t* dev_status, void* stream,
+                         int32_t path);
+
 /* ---------------------------------------------------------------------
  * rerank -- re-order a shortlist by the original vectors (Sec. 5.3: n > k
  * proxy results are re-ordered in the original space and the best k
@@ -169,13 +194,128 @@ int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d
                int64_t* ids, float* scores, int32_t* dev_status, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Resident database (the serving form of the path: a database encoded
+ * once, Sec. 1.1's "pre-processing of S before q becomes available", and
+ * searched by many query batches).
+ *
+ * evp_db_create borrows T ([ns][2W] packed codes, device, 16-byte aligned)
+ * and U ([ns][d] float32 rows, device, or NULL if no rerank is wanted); the
+ * caller keeps both alive and unchanged until evp_db_destroy.  With
+ * EVP_DB_TENSOR_COPY the handle also owns a one-byte-per-element e4m3 copy
+ * of the codes ([ns][Kp], Kp = d rounded up to 128; allocated with
+ * cudaMalloc, filled on `stream`, which is synchronised before returning)
+ * so that the tensor-core scan need not rebuild it per call.
+ * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_UNSUPPORTED (d > EVP_MAX_D_SCAN),
+ * EVP_ERR_NO_MEMORY (the copy could not be allocated) or EVP_ERR_CUDA.
+ *
+ * evp_db_knn: ternary_knn_path against the resident database (same
+ * arguments, same results).
+ *
+ * evp_db_search: the whole path for float32 queries Q [nq][d] (device):
+ * evp_encode -> scan for the n_shortlist nearest by Delta -> rerank of
+ * that shortlist by <q, s> over U -> ids [nq][k] (int64) and scores
+ * [nq][k] (float32), k <= n_shortlist <= min(ns, EVP_MAX_K).  Needs U.
+ * The scan path is chosen as by ternary_knn.
+ *
+ * evp_db_search_host: the same with HOST buffers: Q_host is copied to the
+ * device, results are copied back, all asynchronously on `stream`; the host
+ * buffers must stay valid until the stream has passed the call (pinned
+ * memory makes the copies truly asynchronous).
+ *
+ * Workspaces are caller-owned device memory (256-byte aligned) of at least
+ * the size the matching *_workspace call returns.
+ * ------------------------------------------------------------------- */
+typedef struct evp_db* evp_db_t;
+#define EVP_DB_TENSOR_COPY 1
+
+int32_t evp_db_create(const uint64_t* T, const float* U, int64_t ns, int32_t d, int32_t x,
+                      int32_t flags, void* stream, evp_db_t* out);
+int32_t evp_db_destroy(evp_db_t db);
+int32_t evp_db_dim(evp_db_t db);   /* d of the database (0 for NULL) */
+int64_t evp_db_rows(evp_db_t db);  /* ns of the database (0 for NULL) */
+size_t evp_db_knn_workspace(evp_db_t db, int64_t nq, int32_t k, int32_t path);
+int32_t evp_db_knn(evp_db_t db, const uint64_t* Q, int64_t nq, int32_t k, int64_t* ids,
+                   int32_t* dist, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream,
+                   int32_t path);
+size_t evp_db_search_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k);
+int32_t evp_db_search(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortlist, int32_t k,
+                      int64_t* ids, float* scores, void* ws, size_t ws_bytes,
+                      int32_t* dev_status, void* stream);
+size_t evp_db_search_host_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k);
+int32_t evp_db_search_host(evp_db_t db, const float* Q_host, int64_t nq, int32_t n_shortlist,
+                           int32_t k, int64_t* ids_host, float* scores_host, void* ws,
+                           size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over a resident database
+ * (the served form of the Sec. 5.3 search; the paper has no serving
+ * system).
+ *
+ * evp_server_create starts a host worker thread.  Each request (host
+ * float32 queries Q_host [nq][d], k) is searched exactly as
+ * evp_db_search_host would search it alone, with a shortlist of
+ * min(shortlist_factor * k, EVP_MAX_K) rows by Delta reranked to k: the
+ * worker coalesces pending requests with the same k, in arrival order, into
+ * batches of at most max_batch_queries queries and runs up to `slots`
+ * batches concurrently, each on its own stream with its own pinned staging
+ * and device workspace.  Requests arriving while batches run are admitted
+ * as soon as a slot frees up.  Results are bit-identical whether a request
+ * runs alone or among others.
+ *
+ * Admission by memory: slots = min(max_slots, mem_budget_bytes / bytes of
+ * one slot's workspace) (mem_budget_bytes <= 0 means one slot);
+ * evp_server_create returns EVP_ERR_NO_MEMORY when not even one slot fits,
+ * and evp_server_submit returns EVP_ERR_NO_MEMORY for a request larger than
+ * a slot.
+ *
+ * evp_server_submit copies nothing at submission: Q_host, ids_host
+ * ([nq][k] int64) and scores_host ([nq][k] float32) must stay valid until
+ * evp_server_wait has returned EVP_OK for the request.  evp_server_wait
+ * blocks up to timeout_us microseconds (EVP_ERR_TIMEOUT if the request is
+ * not finished; it can be waited for again) and then releases the request;
+ * *request_status is the device status of the request's batch and
+ * *latency_us the time from submission to completion.  evp_server_stats
+ * reports completed requests, queries, batches, pending requests and the
+ * p50 / p99 / max latency of the requests completed since the last
+ * evp_server_reset_stats.  evp_server_destroy finishes queued requests
+ * (resuming a paused server) and joins the worker.
+ * ------------------------------------------------------------------- */
+typedef struct evp_server* evp_server_t;
+typedef struct {
+    int32_t device;             /* CUDA device holding the database            */
+    int32_t max_batch_queries;  /* capacity of one batch (slot), in queries    */
+    int32_t max_k;              /* largest k a request may ask for             */
+    int32_t shortlist_factor;   /* shortlist length = factor * k (capped)      */
+    int32_t max_slots;          /* batches in flight at most                   */
+    int64_t mem_budget_bytes;   /* device bytes available for slot workspaces  */
+} evp_server_config;
+typedef struct {
+    int64_t requests, queries, batches, pending;
+    double p50_us, p99_us, max_us;
+} evp_server_stats_t;
+
+int32_t evp_server_create(evp_db_t db, const evp_server_config* cfg, evp_server_t* out);
+int32_t evp_server_slots(evp_server_t s);
+int32_t evp_server_submit(evp_server_t s, const float* Q_host, int64_t nq, int32_t k,
+                          int64_t* ids_host, float* scores_host, int64_t* request_id);
+int32_t evp_server_wait(evp_server_t s, int64_t request_id, int64_t timeout_us,
+                        int32_t* request_status, double* latency_us);
+int32_t evp_server_stats(evp_server_t s, evp_server_stats_t* out);
+int32_t evp_server_reset_stats(evp_server_t s);
+/* Stop (1) or resume (0) admitting new batches; batches in flight finish.
+ * Requests keep queueing while paused.  Used to drain, and by tests to
+ * stall the worker on the host. */
+int32_t evp_server_pause(evp_server_t s, int32_t paused);
+int32_t evp_server_destroy(evp_server_t s);
+
+/* ---------------------------------------------------------------------
  * Kernel timing (measurement support; the paper has no counterpart).
  *
  * evp_timing_enable(1) makes every later call record a pair of CUDA events
  * on its stream around each launch of the library's kernels; (0) stops
  * recording.  evp_timing_read synchronises on the recorded events and
  * returns, for the kernel family `name` ("encode", "scan_init",
- * "scan_popc", "final_merge", "rerank"), the number of launches and their total
+ * "scan_popc", "unpack_fp8", "scan_mma", "final_merge", "rerank"), the number of launches and their total
  * duration in milliseconds since the last evp_timing_reset.  Returns
  * EVP_OK, EVP_ERR_INVALID (null outputs) or EVP_ERR_CUDA.  Enabling adds
  * two event records per launch; leave it off outside measurements.

@@ -8,6 +8,19 @@
 
 namespace evp {
 
+EncodeTiledFn encode_tiled_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
 int num_sms() {
     static int cached[64] = {0};
     int dev = 0;
@@ -109,24 +122,59 @@ int32_t evp_encode(const float* U, int64_t n, int32_t d, int32_t x, uint64_t* T,
     return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 
-size_t ternary_knn_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k) {
+}  // extern "C"
+
+namespace {
+
+int resolve_path(int64_t nq, int32_t k, int32_t path) {
+    if (path == EVP_PATH_AUTO) return (nq > 16 && k <= MMA_K_MAX) ? EVP_PATH_MMA : EVP_PATH_POPC;
+    return path;
+}
+
+int32_t check_knn_args(int64_t nq, int64_t ns, int32_t d, int32_t x, int32_t k, int32_t path) {
+    if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
+        (int64_t)k > ns || path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
+        return EVP_ERR_INVALID;
+    if (d > EVP_MAX_D_SCAN || k > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
+    if (resolve_path(nq, k, path) == EVP_PATH_MMA && k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
+    return EVP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ternary_knn_path_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k, int32_t path) {
     if (nq <= 0 || ns <= 0 || d < 1 || k < 1) return 0;
+    if (resolve_path(nq, k, path) == EVP_PATH_MMA)
+        return plan_mma_scan(nq, ns, d, k, /*convert_db=*/true).ws_bytes;
     return plan_popc_scan(nq, ns, d, k).ws_bytes;
+}
+
+size_t ternary_knn_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k) {
+    return ternary_knn_path_workspace(nq, ns, d, k, EVP_PATH_AUTO);
+}
+
+int32_t ternary_knn_path(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns,
+                         int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist, void* ws,
+                         size_t ws_bytes, int32_t* dev_status, void* stream, int32_t path) {
+    const int32_t rc = check_knn_args(nq, ns, d, x, k, path);
+    if (rc != EVP_OK) return rc;
+    if (nq == 0) return EVP_OK;
+    if (!Q || !S || !ids || !dist || !ws) return EVP_ERR_INVALID;
+    if ((reinterpret_cast<uintptr_t>(S) & 15) != 0 || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
+        return EVP_ERR_INVALID;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (resolve_path(nq, k, path) == EVP_PATH_MMA)
+        return run_mma_knn(Q, nq, nullptr, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status, s);
+    return run_popc_knn(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status, s);
 }
 
 int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int32_t d,
                     int32_t x, int32_t k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                     int32_t* dev_status, void* stream) {
-    if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
-        (int64_t)k > ns)
-        return EVP_ERR_INVALID;
-    if (d > EVP_MAX_D_SCAN || k > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
-    if (nq == 0) return EVP_OK;
-    if (!Q || !S || !ids || !dist || !ws) return EVP_ERR_INVALID;
-    if ((reinterpret_cast<uintptr_t>(S) & 15) != 0 || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
-        return EVP_ERR_INVALID;
-    return run_popc_knn(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status,
-                        static_cast<cudaStream_t>(stream));
+    return ternary_knn_path(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status, stream,
+                            EVP_PATH_AUTO);
 }
 
 int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d,

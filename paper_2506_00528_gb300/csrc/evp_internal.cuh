@@ -150,6 +150,14 @@ struct TimedLaunch {
 // ---- launchers (defined in the .cu files, called from api.cu) ----------
 int num_sms();
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library does not link libcuda directly).  nullptr if unavailable.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled_fn();
+
 cudaError_t launch_encode(const float* U, int64_t n, int d, int x, uint64_t* T,
                           int32_t* status, cudaStream_t stream);
 
@@ -165,6 +173,30 @@ ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k);
 int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
                      int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                      int32_t* status, cudaStream_t stream);
+
+// Per-query merge of per-(query, slice) sorted key lists ([nq][nslices][2][k]
+// with meta [nq][nslices] = (length, buffer)) into the k best.
+int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
+                           int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
+                           cudaStream_t stream);
+
+struct MmaPlan {
+    int kp;                 // K padded to a multiple of 128
+    int qtiles;             // 128-query tiles
+    int nslices;            // database slices per query tile
+    int64_t rows_per_slice;
+    size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, ws_bytes;
+};
+constexpr int MMA_K_MAX = 128;  // largest k of the tensor-core path
+int mma_kp(int d);
+MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db);
+cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
+                              cudaStream_t stream);
+// S8: resident e4m3 copy of the database ([ns][kp]) or nullptr, in which case
+// S is converted into the workspace first.
+int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint64_t* S,
+                    int64_t ns, int d, int x, int k, int64_t* ids, int32_t* dist, void* ws,
+                    size_t ws_bytes, int32_t* status, cudaStream_t stream);
 
 cudaError_t launch_rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int d,
                           const int64_t* shortlist, int n, int k, int64_t* ids, float* scores,

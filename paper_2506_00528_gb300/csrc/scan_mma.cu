@@ -1,0 +1,556 @@
+// ternary_knn, tensor-core path: the exhaustive scan as a dense contraction
+// on the 5th-generation tensor cores (tcgen05, kind::f8f6f4).
+//
+// b2sp(q, s) of Sec. 5.1.2 is the scalar product of two ternary vectors.
+// Both operands are written as e4m3 bytes (+1 = 0x38, -1 = 0xB8, 0 = 0x00),
+// which represent {-1, 0, 1} exactly; the tensor core accumulates in
+// float32, where every partial sum is an integer of magnitude <= d < 2^24,
+// so D = Q S^T holds b2sp exactly.  Delta = 2x - 2 b2sp for codes with x
+// non-zeros each.  Float8 is used instead of int8 because the dense int8
+// tensor rate of this GPU generation is far below its fp8 rate.
+//
+// Kernel (one CTA per SM; CTA = one tile of 128 queries x one slice of the
+// database):
+//   warp 0      TMA producer: K-chunks of 128 bytes of the query tile (A,
+//               128 x 128 B) and of the database tile (B, 256 x 128 B),
+//               SWIZZLE_128B, through a ring of STAGES mbarrier stages;
+//   warp 1      allocates 512 TMEM columns, issues tcgen05.mma
+//               (M=128, N=256, K=32) from one thread into one of two
+//               accumulators (256 columns each), commits stage releases and
+//               accumulator-ready signals with tcgen05.commit;
+//   warps 2-5   epilogue: tcgen05.ld of the accumulator (thread = TMEM lane
+//               = query), Delta from D, and a private max-heap of the k best
+//               (Delta/2 << 20 | row-in-slice) keys in shared memory.  A row
+//               is a candidate only if its D beats the heap root (rows arrive
+//               in ascending index order, so an equal Delta never displaces)
+//               and is not worse than the best k-th Delta any other slice of
+//               the same query has published (atomicMin in the workspace).
+//               Each 32-column TMEM load is first reduced to its maximum, so
+//               a warp skips the group when no lane has a candidate;
+//               candidates go to a small per-thread staging buffer, and the
+//               warp inserts all lanes' staged keys into their heaps together
+//               when any lane's buffer fills, so heap updates of different
+//               lanes do not serialise.
+// The Delta matrix is never written to memory.  Per (query, slice) sorted
+// lists go to the workspace and the per-query merge of the popcount path
+// combines them.  Every mbarrier wait is bounded (2 s); on expiry the CTA
+// reports EVP_ERR_TIMEOUT, drains what it issued and frees TMEM.
+#include "evp_internal.cuh"
+
+#include <algorithm>
+
+namespace evp {
+
+namespace {
+
+constexpr int MMA_M = 128;
+constexpr int MMA_N = 256;
+constexpr int MMA_K = 32;
+constexpr int KCHUNK = 128;
+constexpr int STAGES = 3;
+constexpr int HEAP_K_MAX = 128;
+constexpr int NUM_THREADS = 192;
+constexpr int A_STAGE_BYTES = MMA_M * KCHUNK;
+constexpr int B_STAGE_BYTES = MMA_N * KCHUNK;
+constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+constexpr int HEAP_BYTES = HEAP_K_MAX * MMA_M * 4;
+constexpr int STAGE_SLOTS = 16;                     // per-thread candidate staging
+constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
+constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
+constexpr size_t SMEM_BYTES =
+    1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES + STAGING_BYTES + 256;
+
+// Instruction descriptor: D = f32, A = B = e4m3, both K-major, N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4)                  // D format f32
+                           | (0u << 7) | (0u << 10)   // A, B format e4m3
+                           | ((uint32_t)(MMA_N >> 3) << 17) | ((uint32_t)(MMA_M >> 4) << 24);
+
+struct MmaArgs {
+    int nq;
+    int64_t ns;
+    int kchunks;
+    int x;
+    int k;
+    int64_t rows_per_slice;
+    uint64_t* lists;       // [nq][nslices][2][k], buffer 0 used
+    int32_t* meta;         // [nq][nslices][2]
+    uint64_t* tau_global;  // [nq]
+    int32_t* status;
+};
+
+// Shared-memory matrix descriptor of a K-major SWIZZLE_128B tile whose
+// 8-row core groups are 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4)  // start address
+           | (1ull << 16)                       // leading byte offset (unused for SW128 K-major)
+           | (64ull << 32)                      // stride byte offset 1024 >> 4
+           | (1ull << 46)                       // descriptor version
+           | (2ull << 61);                      // SWIZZLE_128B
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Max-heap of u32 keys, element i of thread m at h[i * MMA_M + m].
+__device__ __forceinline__ void heap_sift_down(uint32_t* h, int m, int n, int i) {
+    const uint32_t v = h[i * MMA_M + m];
+    while (true) {
+        int c = 2 * i + 1;
+        if (c >= n) break;
+        uint32_t cv = h[c * MMA_M + m];
+        if (c + 1 < n) {
+            const uint32_t c2 = h[(c + 1) * MMA_M + m];
+            if (c2 > cv) {
+                cv = c2;
+                ++c;
+            }
+        }
+        if (cv <= v) break;
+        h[i * MMA_M + m] = cv;
+        i = c;
+    }
+    h[i * MMA_M + m] = v;
+}
+
+__device__ __forceinline__ void heap_push(uint32_t* h, int m, int n, uint32_t key) {
+    int i = n;
+    while (i > 0) {
+        const int p = (i - 1) >> 1;
+        const uint32_t pv = h[p * MMA_M + m];
+        if (pv >= key) break;
+        h[i * MMA_M + m] = pv;
+        i = p;
+    }
+    h[i * MMA_M + m] = key;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const MmaArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+    uint8_t* stages = smem;
+    uint32_t* heap = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES);
+    uint32_t* staging = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES +
+                                                 STAGING_BYTES);
+    uint64_t* full = bars;                 // [STAGES]
+    uint64_t* empty = bars + STAGES;       // [STAGES]
+    uint64_t* acc_full = bars + 2 * STAGES;      // [2]
+    uint64_t* acc_empty = bars + 2 * STAGES + 2; // [2]
+    uint64_t* done = bars + 2 * STAGES + 4;      // [1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int qt = blockIdx.y, slice = blockIdx.x, nslices = gridDim.x;
+    const int64_t row0 = (int64_t)slice * a.rows_per_slice;
+    const int64_t row_end = min(row0 + a.rows_per_slice, a.ns);
+    const int ntiles = row_end > row0 ? (int)((row_end - row0 + MMA_N - 1) / MMA_N) : 0;
+    const int kchunks = a.kchunks;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&acc_full[b], 1);
+            mbar_init(&acc_empty[b], MMA_M);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            int it = 0;
+            bool ok = true;
+            for (int t = 0; t < ntiles && ok; ++t) {
+                for (int kc = 0; kc < kchunks; ++kc, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u) || *(volatile int*)abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t* st = stages + s * STAGE_BYTES;
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, qt * MMA_M);
+                    tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK,
+                                (int32_t)(row0 + (int64_t)t * MMA_N));
+                }
+            }
+            if (!ok) {
+                report(a.status, EVP_ERR_TIMEOUT);
+                *(volatile int*)abort_flag = 1;
+                // let every stage this thread filled land before the CTA exits
+                for (int j = max(0, it - STAGES); j < it; ++j)
+                    mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            int it = 0;
+            bool ok = true;
+            for (int t = 0; t < ntiles && ok; ++t) {
+                const int b = t & 1;
+                const uint32_t use = (uint32_t)(t >> 1);
+                if (!mbar_wait_bounded(&acc_empty[b], (use & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(b * MMA_N);
+                for (int kc = 0; kc < kchunks; ++kc, ++it) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                    if (!mbar_wait_bounded(&full[s], ph) || *(volatile int*)abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+                    const uint32_t sb = sa + A_STAGE_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < KCHUNK / MMA_K; ++kk) {
+                        mma_f8(dt, sw128_desc(sa + kk * MMA_K), sw128_desc(sb + kk * MMA_K),
+                               (kc > 0 || kk > 0) ? 1u : 0u);
+                    }
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&acc_full[b]);
+            }
+            if (!ok) {
+                report(a.status, EVP_ERR_TIMEOUT);
+                *(volatile int*)abort_flag = 1;
+            }
+            // all issued MMAs complete before TMEM is released
+            mma_commit(done);
+            mbar_wait_bounded(done, 0);
+        }
+    } else {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;
+        const int m = quarter * 32 + lane;  // TMEM lane = query row in the tile
+        const int64_t qrow = (int64_t)qt * MMA_M + m;
+        const bool valid_q = qrow < a.nq;
+        const int k = a.k;
+        uint32_t* tau_half = reinterpret_cast<uint32_t*>(a.tau_global);
+        int hs = 0;
+        float dtau = -INFINITY;   // own heap root: accept D > dtau (strict: rows arrive in order)
+        float dglob = -INFINITY;  // best k-th Delta/2 any slice has published: accept D >= it
+        uint32_t published = 0xFFFFFFFFu;
+        int sc = 0;  // staged candidates of this thread
+        // Insert the staged candidates into the heap.  All lanes of the warp
+        // flush together, so their heap updates run side by side instead of
+        // one lane at a time.
+        auto flush = [&]() {
+            const int cmax = __reduce_max_sync(0xffffffffu, sc);
+            for (int i = 0; i < cmax; ++i) {
+                if (i < sc) {
+                    const uint32_t key = staging[i * MMA_M + m];
+                    if (hs < k) {
+                        heap_push(heap, m, hs, key);
+                        ++hs;
+                    } else if (key < heap[m]) {
+                        heap[m] = key;
+                        heap_sift_down(heap, m, hs, 0);
+                    }
+                }
+            }
+            sc = 0;
+            if (hs == k) dtau = (float)(a.x - (int)(heap[m] >> LOCAL_BITS));
+        };
+        bool ok = true;
+        for (int t = 0; t < ntiles; ++t) {
+            const int b = t & 1;
+            const uint32_t use = (uint32_t)(t >> 1);
+            // one lane waits, the warp follows it (keeps the warp converged)
+            int got = 1;
+            if (lane == 0)
+                got = mbar_wait_bounded(&acc_full[b], use & 1u) && !*(volatile int*)abort_flag;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            if (valid_q) {
+                const uint32_t g = *reinterpret_cast<volatile uint32_t*>(&tau_half[qrow]);
+                if (g != 0xFFFFFFFFu) dglob = (float)(a.x - (int)g) - 0.5f;
+            }
+            const int64_t tile_row = row0 + (int64_t)t * MMA_N;
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * MMA_N);
+            for (int c = 0; c < MMA_N / 32; ++c) {
+                uint32_t v[32];
+                __syncwarp();
+                tmem_ld32(tbase + (uint32_t)(c * 32), v);
+                float mx = __uint_as_float(v[0]);
+#pragma unroll
+                for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(v[j]));
+                float thr = fmaxf(dtau, dglob);
+                if (!__any_sync(0xffffffffu, valid_q && mx > thr)) continue;
+#pragma unroll
+                for (int jc = 0; jc < 4; ++jc) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float dot = __uint_as_float(v[jc * 8 + j]);
+                        const int64_t row = tile_row + c * 32 + jc * 8 + j;
+                        if (valid_q && dot > thr && row < row_end) {
+                            const uint32_t half_delta = (uint32_t)(a.x - __float2int_rn(dot));
+                            staging[sc * MMA_M + m] =
+                                (half_delta << LOCAL_BITS) | (uint32_t)(row - row0);
+                            ++sc;
+                        }
+                    }
+                    if (__any_sync(0xffffffffu, sc > STAGE_SLOTS - 8)) {
+                        flush();
+                        thr = fmaxf(dtau, dglob);
+                    }
+                }
+            }
+            if (hs == k && valid_q) {
+                // share this slice's k-th Delta/2: no row with a larger Delta anywhere
+                // can be among the query's k nearest
+                const uint32_t root_half = heap[m] >> LOCAL_BITS;
+                if (root_half < published) {
+                    atomicMin(&tau_half[qrow], root_half);
+                    published = root_half;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&acc_empty[b]);
+        }
+        if (ok) flush();
+        if (!ok) {
+            report(a.status, EVP_ERR_TIMEOUT);
+            *(volatile int*)abort_flag = 1;
+        } else if (valid_q) {
+            // heap -> ascending order in place, then the (query, slice) list
+            for (int n = hs - 1; n > 0; --n) {
+                const uint32_t top = heap[m];
+                heap[m] = heap[n * MMA_M + m];
+                heap[n * MMA_M + m] = top;
+                heap_sift_down(heap, m, n, 0);
+            }
+            uint64_t* out = a.lists + ((qrow * nslices + slice) * 2) * k;
+            uint64_t last = KEY_NONE;
+            for (int j = 0; j < hs; ++j) {
+                const uint32_t key = heap[j * MMA_M + m];
+                last = ((uint64_t)(2u * (key >> LOCAL_BITS)) << 32) |
+                       (uint64_t)(row0 + (key & ((1u << LOCAL_BITS) - 1u)));
+                out[j] = last;
+            }
+            int32_t* mt = a.meta + (qrow * nslices + slice) * 2;
+            mt[0] = hs;
+            mt[1] = 0;
+            if (hs == k)
+                atomicMin(reinterpret_cast<unsigned long long*>(&a.tau_global[qrow]),
+                          (unsigned long long)last);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// Packed codes -> e4m3 rows [n][Kp] (Kp a multiple of 128; columns >= d are 0).
+__global__ void unpack_fp8_kernel(const uint64_t* __restrict__ T, int64_t n, int W, int Kp,
+                                  uint8_t* __restrict__ out) {
+    const int groups = Kp / 16;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = idx / groups;
+    if (row >= n) return;
+    const int g = (int)(idx - row * groups);
+    const int j0 = g * 16, w = j0 >> 6, sh = j0 & 63;
+    uint32_t p = 0, q = 0;
+    if (w < W) {
+        p = (uint32_t)((T[row * 2 * W + w] >> sh) & 0xFFFFu);
+        q = (uint32_t)((T[row * 2 * W + W + w] >> sh) & 0xFFFFu);
+    }
+    uint32_t o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int e = i * 4 + b;
+            const uint32_t byte = ((p >> e) & 1u) ? 0x38u : (((q >> e) & 1u) ? 0xB8u : 0u);
+            word |= byte << (8 * b);
+        }
+        o[i] = word;
+    }
+    reinterpret_cast<uint4*>(out + row * (int64_t)Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+__global__ void init_tau_n_kernel(uint64_t* tau, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) tau[i] = KEY_NONE;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+int mma_kp(int d) { return (d + KCHUNK - 1) / KCHUNK * KCHUNK; }
+
+MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
+    MmaPlan p{};
+    p.kp = mma_kp(d);
+    p.qtiles = (int)((nq + MMA_M - 1) / MMA_M);
+    const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
+    const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
+    int64_t slices = std::max<int64_t>(1, num_sms() / std::max(1, p.qtiles));
+    slices = std::max(slices, min_slices);
+    slices = std::min(slices, std::max<int64_t>(1, ntiles));
+    const int64_t tiles_per_slice = (ntiles + slices - 1) / slices;
+    p.rows_per_slice = tiles_per_slice * MMA_N;
+    p.nslices = (int)((ns + p.rows_per_slice - 1) / p.rows_per_slice);
+    p.a_bytes = align256((size_t)p.qtiles * MMA_M * p.kp);
+    p.b_bytes = convert_db ? align256((size_t)ns * p.kp) : 0;
+    p.list_bytes = align256((size_t)nq * p.nslices * 2 * k * 8);
+    p.meta_bytes = align256((size_t)nq * p.nslices * 2 * 4);
+    p.tau_bytes = align256((size_t)nq * 8);
+    p.ws_bytes = p.a_bytes + p.b_bytes + p.list_bytes + p.meta_bytes + p.tau_bytes;
+    return p;
+}
+
+cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
+                              cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const int W = (d + 63) / 64, Kp = mma_kp(d);
+    const int64_t threads = n * (Kp / 16);
+    TimedLaunch timer("unpack_fp8", stream);
+    unpack_fp8_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(T, n, W, Kp, out);
+    return cudaGetLastError();
+}
+
+int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint64_t* S,
+                    int64_t ns, int d, int x, int k, int64_t* ids, int32_t* dist, void* ws,
+                    size_t ws_bytes, int32_t* status, cudaStream_t stream) {
+    if (k > HEAP_K_MAX) return EVP_ERR_UNSUPPORTED;
+    const MmaPlan p = plan_mma_scan(nq, ns, d, k, S8 == nullptr);
+    if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    uint8_t* A8 = w;
+    uint8_t* B8 = S8 ? const_cast<uint8_t*>(S8) : w + p.a_bytes;
+    uint64_t* lists = reinterpret_cast<uint64_t*>(w + p.a_bytes + p.b_bytes);
+    int32_t* meta = reinterpret_cast<int32_t*>(w + p.a_bytes + p.b_bytes + p.list_bytes);
+    uint64_t* tau = reinterpret_cast<uint64_t*>(w + p.a_bytes + p.b_bytes + p.list_bytes +
+                                                p.meta_bytes);
+    if ((reinterpret_cast<uintptr_t>(B8) & 255) != 0) return EVP_ERR_INVALID;
+
+    if (launch_unpack_fp8(Q, nq, d, A8, stream) != cudaSuccess) return EVP_ERR_CUDA;
+    if (!S8 && launch_unpack_fp8(S, ns, d, B8, stream) != cudaSuccess) return EVP_ERR_CUDA;
+    {
+        TimedLaunch timer("scan_init", stream);
+        init_tau_n_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(tau, (int)nq);
+    }
+
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return EVP_ERR_CUDA;
+    CUtensorMap tmA, tmB;
+    cuuint64_t gdimA[2] = {(cuuint64_t)p.kp, (cuuint64_t)nq};
+    cuuint64_t gdimB[2] = {(cuuint64_t)p.kp, (cuuint64_t)ns};
+    cuuint64_t gstride[1] = {(cuuint64_t)p.kp};
+    cuuint32_t boxA[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)MMA_M};
+    cuuint32_t boxB[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)MMA_N};
+    cuuint32_t es[2] = {1, 1};
+    if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, A8, gdimA, gstride, boxA, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return EVP_ERR_CUDA;
+    if (enc(&tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, B8, gdimB, gstride, boxB, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return EVP_ERR_CUDA;
+
+    MmaArgs args{};
+    args.nq = (int)nq;
+    args.ns = ns;
+    args.kchunks = p.kp / KCHUNK;
+    args.x = x;
+    args.k = k;
+    args.rows_per_slice = p.rows_per_slice;
+    args.lists = lists;
+    args.meta = meta;
+    args.tau_global = tau;
+    args.status = status;
+    if (cudaFuncSetAttribute(scan_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)SMEM_BYTES) != cudaSuccess)
+        return EVP_ERR_CUDA;
+    {
+        TimedLaunch timer("scan_mma", stream);
+        scan_mma_kernel<<<dim3(p.nslices, p.qtiles), NUM_THREADS, SMEM_BYTES, stream>>>(tmA, tmB,
+                                                                                       args);
+    }
+    if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
+    return launch_final_merge(lists, meta, tau, nq, p.nslices, k, ids, dist, stream);
+}
+
+}  // namespace evp

@@ -44,7 +44,10 @@ constexpr int MERGE_AT = CAND_CAP - SCAN_ROWS;  // merge before a tile could ove
 constexpr int QB_MAX = 16;
 constexpr int MAX_STAGES = 4;
 constexpr int SMEM_BUDGET = 225 * 1024;
-constexpr int FM_WARPS = 4;                     // final merge: queries per CTA
+constexpr int FM_THREADS = 256;                 // final merge: one CTA per query
+constexpr int FM_MAX_SLICES = 1024;             // slice lists per query in the final merge
+constexpr int FM_OUT_BYTES = EVP_MAX_K * 8;     // sorted output keys
+constexpr int FM_STAGE_BYTES = 160 * 1024;      // lists staged in shared memory up to this size
 
 struct ScanArgs {
     const uint64_t* Q;  // this pass's query codes [nqg][2W]
@@ -70,12 +73,14 @@ struct SmemLayout {
     size_t stage_bytes, qv_off, cand_off, tau_off, cnt_off, bar_off, flag_off, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(int W, int stages) {
+// Shared-memory carve-up for a pass of `qb` queries (candidate buffers are
+// sized by the pass, so small passes leave room for more TMA stages).
+__host__ __device__ inline SmemLayout smem_layout(int W, int stages, int qb) {
     SmemLayout L;
     L.stage_bytes = align_up((size_t)SCAN_ROWS * row_pitch_words(W) * 8, 1024);
     L.qv_off = L.stage_bytes * stages;
     L.cand_off = L.qv_off + align_up((size_t)QB_MAX * W * 16, 128);
-    L.tau_off = L.cand_off + (size_t)QB_MAX * CAND_CAP * 8;
+    L.tau_off = L.cand_off + (size_t)qb * CAND_CAP * 8;
     L.cnt_off = L.tau_off + QB_MAX * 8;
     L.bar_off = L.cnt_off + align_up(3 * QB_MAX * 4, 8);
     L.flag_off = L.bar_off + MAX_STAGES * 8;
@@ -93,7 +98,7 @@ template <int QB>
 __global__ void __launch_bounds__(SCAN_ROWS, 1)
 scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const SmemLayout L = smem_layout(a.W, a.stages);
+    const SmemLayout L = smem_layout(a.W, a.stages, QB);
     uint64_t* qv = reinterpret_cast<uint64_t*>(smem + L.qv_off);
     uint64_t* cand = reinterpret_cast<uint64_t*>(smem + L.cand_off);
     uint64_t* tau = reinterpret_cast<uint64_t*>(smem + L.tau_off);
@@ -253,76 +258,118 @@ __global__ void init_tau_kernel(uint64_t* tau_global) {
     if (threadIdx.x < QB_MAX) tau_global[threadIdx.x] = KEY_NONE;
 }
 
-// Per query (one warp): the keys of all slice lists that do not exceed the
-// final global threshold, merged into the k best.
-__global__ void __launch_bounds__(FM_WARPS * 32)
+// Per query (one CTA): the k smallest keys of the union of the per-slice
+// sorted lists.  The k-th smallest key T of the union is found bit by bit
+// from the top (the smallest T with count(key <= T) >= k), each count being
+// a sum of per-list binary searches; then every list contributes its prefix
+// of keys <= T (exactly k keys in all, keys being distinct) and those k keys
+// are sorted.  Lists are staged in shared memory when they fit.
+__device__ __forceinline__ int upper_bound_u64(const uint64_t* a, int n, uint64_t key) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(FM_THREADS)
 final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
-                   const uint64_t* __restrict__ tau_global, int nqg, int nslices, int k,
+                   int nslices, int k, int key_bits, int stage_lists,
                    int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int q = blockIdx.x * FM_WARPS + warp;
-    if (q >= nqg) return;
-    uint64_t* C = reinterpret_cast<uint64_t*>(smem) + (size_t)warp * (CAND_CAP + 2 * k);
-    uint64_t* Lb = C + CAND_CAP;
-    const uint64_t tau_f = tau_global[q];
-    const unsigned lt = (1u << lane) - 1u;
-    int nl = 0, c = 0, nc = 0;
+    __shared__ int red[FM_THREADS / 32];
+    __shared__ int total_s;
+    uint64_t* out = reinterpret_cast<uint64_t*>(smem);           // next_pow2(k) keys
+    int* lens = reinterpret_cast<int*>(smem + FM_OUT_BYTES);     // nslices
+    int* offs = lens + FM_MAX_SLICES;                            // nslices
+    uint64_t* staged = reinterpret_cast<uint64_t*>(smem + FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t q = blockIdx.x;
+    const int64_t qbase = q * nslices;
 
-    auto flush = [&]() {
-        const int P = next_pow2(nc);
-        for (int i = nc + lane; i < P; i += 32) C[i] = KEY_NONE;
-        __syncwarp();
-        warp_bitonic_sort(C, P);
-        nl = warp_merge_topk(Lb + c * k, nl, C, nc, Lb + (c ^ 1) * k, k);
-        c ^= 1;
-        nc = 0;
-        __syncwarp();
+    for (int s = tid; s < nslices; s += FM_THREADS) lens[s] = meta[(qbase + s) * 2];
+    __syncthreads();
+    if (stage_lists) {
+        for (int64_t e = tid; e < (int64_t)nslices * k; e += FM_THREADS) {
+            const int s = (int)(e / k), i = (int)(e - (int64_t)s * k);
+            if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k + i];
+        }
+        __syncthreads();
+    }
+    auto list_ptr = [&](int s) -> const uint64_t* {
+        return stage_lists ? staged + (int64_t)s * k
+                           : lists + ((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k;
     };
-
-    for (int s = 0; s < nslices; ++s) {
-        const int32_t* m = meta + ((int64_t)q * nslices + s) * 2;
-        const int ln = m[0];
-        const uint64_t* src = lists + (((int64_t)q * nslices + s) * 2 + m[1]) * k;
-        for (int b = 0; b < ln; b += 32) {
-            const int i = b + lane;
-            const uint64_t key = i < ln ? src[i] : KEY_NONE;
-            const bool ok = key != KEY_NONE && key <= tau_f;
-            const unsigned bal = __ballot_sync(0xffffffffu, ok);
-            if (ok) C[nc + __popc(bal & lt)] = key;
-            nc += __popc(bal);
-            if (nc > CAND_CAP - 32) flush();
+    auto count_le = [&](uint64_t v) -> int {
+        int c = 0;
+        for (int s = tid; s < nslices; s += FM_THREADS) c += upper_bound_u64(list_ptr(s), lens[s], v);
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) red[warp] = c;
+        __syncthreads();
+        int t = 0;
+#pragma unroll
+        for (int w = 0; w < FM_THREADS / 32; ++w) t += red[w];
+        __syncthreads();
+        return t;
+    };
+    // smallest T with count(key <= T) >= k
+    uint64_t T = 0;
+    for (int b = key_bits - 1; b >= 0; --b) {
+        const uint64_t lowmax = T | ((1ull << b) - 1ull);
+        if (count_le(lowmax) < k) T |= 1ull << b;
+    }
+    // each list's prefix of keys <= T, gathered at exclusive-scan offsets
+    for (int s = tid; s < nslices; s += FM_THREADS) offs[s] = upper_bound_u64(list_ptr(s), lens[s], T);
+    __syncthreads();
+    if (tid == 0) {
+        int run = 0;
+        for (int s = 0; s < nslices; ++s) {
+            const int c = offs[s];
+            offs[s] = run;
+            run += c;
+        }
+        total_s = run;
+    }
+    __syncthreads();
+    const int n = min(total_s, k);
+    int P = 2;
+    while (P < k) P <<= 1;
+    for (int i = tid; i < P; i += FM_THREADS) out[i] = KEY_NONE;
+    __syncthreads();
+    for (int s = tid; s < nslices; s += FM_THREADS) {
+        const uint64_t* L = list_ptr(s);
+        const int o = offs[s];
+        const int c = upper_bound_u64(L, lens[s], T);
+        for (int i = 0; i < c && o + i < k; ++i) out[o + i] = L[i];
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (int i = tid; i < P; i += FM_THREADS) {
+                const int ixj = i ^ jj;
+                if (ixj > i) {
+                    const uint64_t a = out[i], b = out[ixj];
+                    if ((a > b) == ((i & kk) == 0)) {
+                        out[i] = b;
+                        out[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
         }
     }
-    if (nc > 0) flush();
-    for (int j = lane; j < k; j += 32) {
-        const uint64_t key = j < nl ? Lb[c * k + j] : KEY_NONE;
-        ids[(int64_t)q * k + j] = key == KEY_NONE ? -1 : (int64_t)(key & 0xffffffffull);
-        dist[(int64_t)q * k + j] = key == KEY_NONE ? -1 : (int32_t)(key >> 32);
+    for (int j = tid; j < k; j += FM_THREADS) {
+        const uint64_t key = j < n ? out[j] : KEY_NONE;
+        ids[q * k + j] = key == KEY_NONE ? -1 : (int64_t)(key & 0xffffffffull);
+        dist[q * k + j] = key == KEY_NONE ? -1 : (int32_t)(key >> 32);
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_tiled_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiledFn>(p);
-    }
-    return fn;
-}
-
-int choose_stages(int W) {
+int choose_stages(int W, int qb) {
     for (int st = MAX_STAGES; st >= 2; --st)
-        if (smem_layout(W, st).total <= (size_t)SMEM_BUDGET) return st;
+        if (smem_layout(W, st, qb).total <= (size_t)SMEM_BUDGET) return st;
     return 0;
 }
 
@@ -339,6 +386,26 @@ cudaError_t launch_scan(const CUtensorMap& tmap, const ScanArgs& a, int nslices,
 }
 
 }  // namespace
+
+int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
+                           int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
+                           cudaStream_t stream) {
+    (void)tau;
+    if (nq <= 0) return EVP_OK;
+    if (nslices > FM_MAX_SLICES) return EVP_ERR_UNSUPPORTED;
+    const size_t list_bytes = (size_t)nslices * k * 8;
+    const int stage = list_bytes <= (size_t)FM_STAGE_BYTES ? 1 : 0;
+    const size_t smem = FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4 + (stage ? list_bytes : 0);
+    if (cudaFuncSetAttribute(final_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4 + FM_STAGE_BYTES) != cudaSuccess)
+        return EVP_ERR_CUDA;
+    // keys are (Delta << 32 | row) with Delta <= 4 * EVP_MAX_D_SCAN
+    const int key_bits = 32 + 13;
+    TimedLaunch timer("final_merge", stream);
+    final_merge_kernel<<<(unsigned)nq, FM_THREADS, smem, stream>>>(lists, meta, nslices, k,
+                                                                   key_bits, stage, ids, dist);
+    return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
 
 ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k) {
     ScanPlan p{};
@@ -361,9 +428,7 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
     const int W = (d + 63) / 64;
     const ScanPlan p = plan_popc_scan(nq, ns, d, k);
     if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
-    const int stages = choose_stages(W);
-    if (stages == 0) return EVP_ERR_UNSUPPORTED;
-    const SmemLayout L = smem_layout(W, stages);
+    if (choose_stages(W, QB_MAX) == 0) return EVP_ERR_UNSUPPORTED;
 
     EncodeTiledFn enc = encode_tiled_fn();
     if (!enc) return EVP_ERR_CUDA;
@@ -385,7 +450,6 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
     a.W = W;
     a.k = k;
     a.pitch = pitch;
-    a.stages = stages;
     a.ntiles = (ns + SCAN_ROWS - 1) / SCAN_ROWS;
     a.tiles_per_slice = (a.ntiles + num_sms() - 1) / num_sms();
     a.lists = reinterpret_cast<uint64_t*>(wsb);
@@ -393,16 +457,15 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
     a.tau_global = reinterpret_cast<uint64_t*>(wsb + p.ws_bytes - 256);
     a.status = status;
 
-    const size_t fm_smem = (size_t)FM_WARPS * (CAND_CAP + 2 * k) * 8;
-    if (cudaFuncSetAttribute(final_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             FM_WARPS * (CAND_CAP + 2 * EVP_MAX_K) * 8) != cudaSuccess)
-        return EVP_ERR_CUDA;
 
     for (int g = 0; g < p.groups; ++g) {
         const int64_t q0 = (int64_t)g * QB_MAX;
         const int nqg = (int)std::min<int64_t>(QB_MAX, nq - q0);
         a.Q = Q + q0 * 2 * W;
         a.nqg = nqg;
+        const int qb = nqg <= 1 ? 1 : nqg <= 2 ? 2 : nqg <= 4 ? 4 : nqg <= 8 ? 8 : 16;
+        a.stages = choose_stages(W, qb);
+        const SmemLayout L = smem_layout(W, a.stages, qb);
         {
             TimedLaunch timer("scan_init", stream);
             init_tau_kernel<<<1, 32, 0, stream>>>(a.tau_global);
@@ -414,13 +477,9 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
         else if (nqg <= 8) e = launch_scan<8>(tmap, a, p.nslices, L.total, stream);
         else e = launch_scan<16>(tmap, a, p.nslices, L.total, stream);
         if (e != cudaSuccess) return EVP_ERR_CUDA;
-        {
-            TimedLaunch timer("final_merge", stream);
-            final_merge_kernel<<<(nqg + FM_WARPS - 1) / FM_WARPS, FM_WARPS * 32, fm_smem,
-                                 stream>>>(a.lists, a.meta, a.tau_global, nqg, p.nslices, k,
-                                           ids + q0 * k, dist + q0 * k);
-        }
-        if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
+        const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, nqg, p.nslices, k,
+                                              ids + q0 * k, dist + q0 * k, stream);
+        if (rc != EVP_OK) return rc;
     }
     return EVP_OK;
 }

@@ -27,6 +27,9 @@ EVP_ERR_CUDA = 5
 EVP_ERR_UNSUPPORTED = 6
 EVP_ERR_RANGE = 7
 
+PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
+MMA_MAX_K = 128
+
 MAX_D_ENCODE = 2048
 MAX_D_SCAN = 1024
 MAX_K = 1024
@@ -46,7 +49,29 @@ SIGNATURES = {
     "evp_encode": (_i32, [_p, _i64, _i32, _i32, _p, _p, _p]),
     "ternary_knn_workspace": (_sz, [_i64, _i64, _i32, _i32]),
     "ternary_knn": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
+    "ternary_knn_path_workspace": (_sz, [_i64, _i64, _i32, _i32, _i32]),
+    "ternary_knn_path": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _sz, _p, _p,
+                                _i32]),
     "rerank": (_i32, [_p, _i64, _p, _i64, _i32, _p, _i32, _i32, _p, _p, _p, _p]),
+    "evp_db_create": (_i32, [_p, _p, _i64, _i32, _i32, _i32, _p, ctypes.POINTER(_p)]),
+    "evp_db_destroy": (_i32, [_p]),
+    "evp_db_knn_workspace": (_sz, [_p, _i64, _i32, _i32]),
+    "evp_db_knn": (_i32, [_p, _p, _i64, _i32, _p, _p, _p, _sz, _p, _p, _i32]),
+    "evp_db_search_workspace": (_sz, [_p, _i64, _i32, _i32]),
+    "evp_db_search": (_i32, [_p, _p, _i64, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
+    "evp_db_search_host_workspace": (_sz, [_p, _i64, _i32, _i32]),
+    "evp_db_search_host": (_i32, [_p, _p, _i64, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
+    "evp_db_dim": (_i32, [_p]),
+    "evp_db_rows": (_i64, [_p]),
+    "evp_server_create": (_i32, [_p, _p, ctypes.POINTER(_p)]),
+    "evp_server_slots": (_i32, [_p]),
+    "evp_server_submit": (_i32, [_p, _p, _i64, _i32, _p, _p, ctypes.POINTER(_i64)]),
+    "evp_server_wait": (_i32, [_p, _i64, _i64, ctypes.POINTER(_i32),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "evp_server_stats": (_i32, [_p, _p]),
+    "evp_server_reset_stats": (_i32, [_p]),
+    "evp_server_pause": (_i32, [_p, _i32]),
+    "evp_server_destroy": (_i32, [_p]),
     "evp_timing_enable": (_i32, [_i32]),
     "evp_timing_reset": (_i32, []),
     "evp_timing_read": (_i32, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -134,14 +159,14 @@ def encode(U: torch.Tensor, x: int, out: torch.Tensor | None = None,
     return out
 
 
-def knn_workspace_bytes(nq: int, ns: int, d: int, k: int) -> int:
-    return int(load().ternary_knn_workspace(int(nq), int(ns), int(d), int(k)))
+def knn_workspace_bytes(nq: int, ns: int, d: int, k: int, path: int = PATH_AUTO) -> int:
+    return int(load().ternary_knn_path_workspace(int(nq), int(ns), int(d), int(k), int(path)))
 
 
 def ternary_knn(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
                 ids: torch.Tensor | None = None, dist: torch.Tensor | None = None,
                 ws: torch.Tensor | None = None, status: torch.Tensor | None = None,
-                stream=None):
+                stream=None, path: int = PATH_AUTO):
     """ternary_knn: packed Q [nq, 2W], packed S [ns, 2W] -> ids int64, dist int32 [nq, k]."""
     _req(Q, torch.int64, "Q")
     _req(S, torch.int64, "S")
@@ -150,11 +175,17 @@ def ternary_knn(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
         ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
     if dist is None:
         dist = torch.empty((nq, k), dtype=torch.int32, device=Q.device)
-    need = knn_workspace_bytes(nq, ns, d, k)
+    need = knn_workspace_bytes(nq, ns, d, k, path)
     if ws is None or ws.numel() < need:
         ws = torch.empty(max(need, 256), dtype=torch.uint8, device=Q.device)
-    rc = load().ternary_knn(_ptr(Q), nq, _ptr(S), ns, int(d), int(x), int(k), _ptr(ids),
-                            _ptr(dist), _ptr(ws), ws.numel(), _ptr(status), _stream_handle(stream))
+    if path == PATH_AUTO:
+        rc = load().ternary_knn(_ptr(Q), nq, _ptr(S), ns, int(d), int(x), int(k), _ptr(ids),
+                                _ptr(dist), _ptr(ws), ws.numel(), _ptr(status),
+                                _stream_handle(stream))
+    else:
+        rc = load().ternary_knn_path(_ptr(Q), nq, _ptr(S), ns, int(d), int(x), int(k),
+                                     _ptr(ids), _ptr(dist), _ptr(ws), ws.numel(), _ptr(status),
+                                     _stream_handle(stream), int(path))
     _check(rc, "ternary_knn")
     return ids, dist
 
@@ -193,3 +224,167 @@ def timing_read(name: str):
     _check(load().evp_timing_read(name.encode(), ctypes.byref(n), ctypes.byref(ms)),
            "evp_timing_read")
     return int(n.value), float(ms.value)
+
+
+class Database:
+    """Resident database handle (evp_db_*): packed codes T [ns, 2W] (int64
+    bits) and optional float rows U [ns, d] stay on the device; the handle
+    keeps references to both so they outlive it."""
+
+    def __init__(self, T: torch.Tensor, U: torch.Tensor | None, d: int, x: int,
+                 tensor_copy: bool = True, stream=None):
+        _req(T, torch.int64, "T")
+        if U is not None:
+            _req(U, torch.float32, "U")
+        self.T, self.U, self.d, self.x = T, U, int(d), int(x)
+        self.ns = T.shape[0]
+        h = ctypes.c_void_p()
+        rc = load().evp_db_create(_ptr(T), _ptr(U), self.ns, self.d, self.x,
+                                  1 if tensor_copy else 0, _stream_handle(stream), ctypes.byref(h))
+        _check(rc, "evp_db_create")
+        self.handle = h
+        self._ws = None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().evp_db_destroy(self.handle), "evp_db_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _workspace(self, need: int, ws):
+        if ws is not None and ws.numel() >= need:
+            return ws
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.T.device)
+        return self._ws
+
+    def knn(self, Q: torch.Tensor, k: int, ids=None, dist=None, ws=None, status=None,
+            stream=None, path: int = PATH_AUTO):
+        _req(Q, torch.int64, "Q")
+        nq = Q.shape[0]
+        ids = ids if ids is not None else torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        dist = dist if dist is not None else torch.empty((nq, k), dtype=torch.int32, device=Q.device)
+        need = int(load().evp_db_knn_workspace(self.handle, nq, int(k), int(path)))
+        ws = self._workspace(need, ws)
+        rc = load().evp_db_knn(self.handle, _ptr(Q), nq, int(k), _ptr(ids), _ptr(dist),
+                               _ptr(ws), ws.numel(), _ptr(status), _stream_handle(stream),
+                               int(path))
+        _check(rc, "evp_db_knn")
+        return ids, dist
+
+    def search_workspace_bytes(self, nq: int, n_shortlist: int, k: int) -> int:
+        return int(load().evp_db_search_workspace(self.handle, nq, int(n_shortlist), int(k)))
+
+    def search(self, Q: torch.Tensor, n_shortlist: int, k: int, ids=None, scores=None, ws=None,
+               status=None, stream=None):
+        """encode -> scan (n_shortlist by Delta) -> rerank (k by <q, s>)."""
+        _req(Q, torch.float32, "Q")
+        nq = Q.shape[0]
+        ids = ids if ids is not None else torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+        scores = scores if scores is not None else torch.empty((nq, k), dtype=torch.float32,
+                                                               device=Q.device)
+        ws = self._workspace(self.search_workspace_bytes(nq, n_shortlist, k), ws)
+        rc = load().evp_db_search(self.handle, _ptr(Q), nq, int(n_shortlist), int(k), _ptr(ids),
+                                  _ptr(scores), _ptr(ws), ws.numel(), _ptr(status),
+                                  _stream_handle(stream))
+        _check(rc, "evp_db_search")
+        return ids, scores
+
+    def search_host_workspace_bytes(self, nq: int, n_shortlist: int, k: int) -> int:
+        return int(load().evp_db_search_host_workspace(self.handle, nq, int(n_shortlist), int(k)))
+
+    def search_host(self, Q_host: torch.Tensor, n_shortlist: int, k: int, ids_host: torch.Tensor,
+                    scores_host: torch.Tensor, ws=None, status=None, stream=None):
+        """The same path with host (preferably pinned) buffers; asynchronous."""
+        if Q_host.is_cuda or Q_host.dtype != torch.float32 or not Q_host.is_contiguous():
+            raise ValueError("Q_host must be a contiguous host float32 tensor")
+        nq = Q_host.shape[0]
+        ws = self._workspace(self.search_host_workspace_bytes(nq, n_shortlist, k), ws)
+        rc = load().evp_db_search_host(self.handle, _ptr(Q_host), nq, int(n_shortlist), int(k),
+                                       _ptr(ids_host), _ptr(scores_host), _ptr(ws), ws.numel(),
+                                       _ptr(status), _stream_handle(stream))
+        _check(rc, "evp_db_search_host")
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_batch_queries", ctypes.c_int32),
+                ("max_k", ctypes.c_int32), ("shortlist_factor", ctypes.c_int32),
+                ("max_slots", ctypes.c_int32), ("mem_budget_bytes", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("requests", ctypes.c_int64), ("queries", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double),
+                ("max_us", ctypes.c_double)]
+
+
+class Server:
+    """Continuous-batching request loop (evp_server_*) over a Database."""
+
+    def __init__(self, db: "Database", max_batch_queries: int = 1024, max_k: int = 100,
+                 shortlist_factor: int = 10, max_slots: int = 3, mem_budget_bytes: int = 0,
+                 device: int | None = None):
+        self.db = db
+        cfg = ServerConfig(device if device is not None else db.T.device.index or 0,
+                           max_batch_queries, max_k, shortlist_factor, max_slots,
+                           mem_budget_bytes)
+        h = ctypes.c_void_p()
+        _check(load().evp_server_create(db.handle, ctypes.byref(cfg), ctypes.byref(h)),
+               "evp_server_create")
+        self.handle = h
+        self._live = {}
+
+    @property
+    def slots(self) -> int:
+        return int(load().evp_server_slots(self.handle))
+
+    def submit(self, Q_host, k: int) -> int:
+        """Queue float32 host queries [nq, d]; returns a request id."""
+        Q = torch.as_tensor(Q_host)
+        if Q.is_cuda or Q.dtype != torch.float32 or not Q.is_contiguous():
+            raise ValueError("Q_host must be a contiguous host float32 tensor or array")
+        nq = Q.shape[0]
+        ids = torch.empty((nq, k), dtype=torch.int64)
+        sc = torch.empty((nq, k), dtype=torch.float32)
+        rid = ctypes.c_int64(0)
+        _check(load().evp_server_submit(self.handle, _ptr(Q), nq, int(k), _ptr(ids), _ptr(sc),
+                                        ctypes.byref(rid)), "evp_server_submit")
+        self._live[rid.value] = (Q, ids, sc)
+        return int(rid.value)
+
+    def wait(self, rid: int, timeout_s: float = 30.0):
+        """(ids, scores, status, latency_us); raises EvpError(EVP_ERR_TIMEOUT) on timeout."""
+        st = ctypes.c_int32(0)
+        lat = ctypes.c_double(0.0)
+        _check(load().evp_server_wait(self.handle, int(rid), int(timeout_s * 1e6),
+                                      ctypes.byref(st), ctypes.byref(lat)), "evp_server_wait")
+        _, ids, sc = self._live.pop(int(rid))
+        return ids, sc, int(st.value), float(lat.value)
+
+    def pause(self, paused: bool = True):
+        _check(load().evp_server_pause(self.handle, 1 if paused else 0), "evp_server_pause")
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().evp_server_stats(self.handle, ctypes.byref(s)), "evp_server_stats")
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def reset_stats(self):
+        _check(load().evp_server_reset_stats(self.handle), "evp_server_reset_stats")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().evp_server_destroy(self.handle), "evp_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -9,16 +9,23 @@ from paper_2506_00528_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def _run(evp, Tq, Ts, d, x, k, dev):
+PATHS = [1, 2]   # EVP_PATH_POPC, EVP_PATH_MMA
+
+
+def _run(evp, Tq, Ts, d, x, k, dev, path=0):
+    if path == 2 and k > 128:
+        pytest.skip("tensor-core path takes k <= 128")
     st = evp.new_status(dev)
     ids, dist = evp.ternary_knn(torch.from_numpy(Tq.view(np.int64)).to(dev),
-                                torch.from_numpy(Ts.view(np.int64)).to(dev), d, x, k, status=st)
+                                torch.from_numpy(Ts.view(np.int64)).to(dev), d, x, k, status=st,
+                                path=path)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     return ids.cpu().numpy(), dist.cpu().numpy()
 
 
-def test_tiny_config_bit_exact(evp_lib, dev):
+@pytest.mark.parametrize("path", PATHS)
+def test_tiny_config_bit_exact(evp_lib, dev, path):
     """The small workload: 10,000 x 384 database, 100 queries, 64-centre
     mixture (sigma 0.5), x = 128, k = 10."""
     d, x, k = 384, 128, 10
@@ -29,7 +36,7 @@ def test_tiny_config_bit_exact(evp_lib, dev):
     st = evp_lib.new_status(dev)
     Ts = evp_lib.encode(torch.from_numpy(U).to(dev), x, status=st)
     Tq = evp_lib.encode(torch.from_numpy(Qf).to(dev), x, status=st)
-    ids, dist = evp_lib.ternary_knn(Tq, Ts, d, x, k, status=st)
+    ids, dist = evp_lib.ternary_knn(Tq, Ts, d, x, k, status=st, path=path)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     np.testing.assert_array_equal(Ts.cpu().numpy().view(np.uint64), oracle.pack(Vs))
@@ -38,69 +45,76 @@ def test_tiny_config_bit_exact(evp_lib, dev):
     np.testing.assert_array_equal(dist.cpu().numpy(), od)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("d", [1, 2, 63, 64, 65, 100, 127, 129, 384, 1000, 1024])
-def test_shapes_across_d(evp_lib, dev, d):
+def test_shapes_across_d(evp_lib, dev, d, path):
     x = oracle.default_x(d)
     ns = 3001
     Vs = synth.ternary_random(ns, d, x, stream=200 + d)
     Vq = synth.ternary_random(5, d, x, stream=300 + d)
     k = min(50, ns)
-    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path)
     oi, od = oracle.knn(Vq, Vs, k)
     np.testing.assert_array_equal(dist, od)
     np.testing.assert_array_equal(ids, oi)
 
 
+@pytest.mark.parametrize("path", PATHS)
 @pytest.mark.parametrize("ns,k", [(1, 1), (255, 255), (256, 17), (257, 257), (1000, 1000),
-                                  (5000, 1), (5000, 1024), (70_001, 100)])
-def test_sizes_and_k(evp_lib, dev, ns, k):
+                                  (5000, 1), (5000, 1024), (70_001, 100),
+                                  (70_001, 1024)])
+def test_sizes_and_k(evp_lib, dev, ns, k, path):
     d, x = 96, 64
     U = synth.mixture_numpy(ns, d, n_centres=16, stream=400)
     Qf = synth.mixture_numpy(7, d, n_centres=16, stream=401)
     Vs, Vq = oracle.encode(U, x), oracle.encode(Qf, x)
-    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path)
     oi, od = oracle.knn(Vq, Vs, k)
     np.testing.assert_array_equal(dist, od)
     np.testing.assert_array_equal(ids, oi)
 
 
-@pytest.mark.parametrize("nq", [1, 2, 3, 15, 16, 17, 33, 50])
-def test_query_counts_span_passes(evp_lib, dev, nq):
+@pytest.mark.parametrize("path", [0] + PATHS)
+@pytest.mark.parametrize("nq", [1, 2, 3, 15, 16, 17, 33, 50, 127, 128, 129, 300])
+def test_query_counts_span_passes(evp_lib, dev, nq, path):
     d, x, k = 256, 171, 20
     U = synth.mixture_numpy(20_000, d, n_centres=32, stream=500)
     Qf = synth.mixture_numpy(nq, d, n_centres=32, stream=501)
     Vs, Vq = oracle.encode(U, x), oracle.encode(Qf, x)
-    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path)
     oi, od = oracle.knn(Vq, Vs, k)
     np.testing.assert_array_equal(dist, od)
     np.testing.assert_array_equal(ids, oi)
 
 
-def test_massive_ties(evp_lib, dev):
+@pytest.mark.parametrize("path,k", [(1, 300), (2, 128), (1, 1024)])
+def test_massive_ties(evp_lib, dev, path, k):
     """Only six distinct codes in the database: almost every Delta ties, so
     the (Delta, index) order decides everything, across slices and merges."""
-    d, x, k = 128, 40, 300
+    d, x = 128, 40
     base = synth.ternary_random(6, d, x, stream=600)
     rng = np.random.default_rng(11)
     Vs = base[rng.integers(0, 6, size=60_000)]
     Vq = np.concatenate([base[:3], synth.ternary_random(4, d, x, stream=601)])
-    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path)
     oi, od = oracle.knn(Vq, Vs, k)
     np.testing.assert_array_equal(dist, od)
     np.testing.assert_array_equal(ids, oi)
 
 
-def test_identical_database(evp_lib, dev):
+@pytest.mark.parametrize("path", PATHS)
+def test_identical_database(evp_lib, dev, path):
     d, x = 64, 10
     Vs = np.repeat(synth.ternary_random(1, d, x, stream=602), 9000, axis=0)
     Vq = synth.ternary_random(3, d, x, stream=603)
-    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, 64, dev)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, 64, dev, path)
     assert np.all(ids == np.arange(64)[None, :])
     oi, od = oracle.knn(Vq, Vs[:100], 64)
     np.testing.assert_array_equal(dist, od)
 
 
-def test_descending_stream_worst_case(evp_lib, dev):
+@pytest.mark.parametrize("path", PATHS)
+def test_descending_stream_worst_case(evp_lib, dev, path):
     """Rows ordered so that each is nearer than all earlier ones: every row
     enters the candidate buffers (the merge path under maximum pressure)."""
     d, x, k = 64, 32, 100
@@ -113,7 +127,7 @@ def test_descending_stream_worst_case(evp_lib, dev):
         v[32:32 + (32 - m)] = 1
         rows.append(v)
     Vs = np.repeat(np.array(rows[::1]), 400, axis=0)      # Delta falls as the index grows
-    ids, dist = _run(evp_lib, oracle.pack(q), oracle.pack(Vs), d, x, k, dev)
+    ids, dist = _run(evp_lib, oracle.pack(q), oracle.pack(Vs), d, x, k, dev, path)
     oi, od = oracle.knn(q, Vs, k)
     np.testing.assert_array_equal(dist, od)
     np.testing.assert_array_equal(ids, oi)
@@ -128,6 +142,11 @@ def test_argument_errors(evp_lib, dev):
     big = torch.zeros((10, 34), dtype=torch.int64, device=dev)
     with pytest.raises(evp_lib.EvpError):
         evp_lib.ternary_knn(big[:1], big, 2048, 10, 3)         # d above the scan limit
+    with pytest.raises(evp_lib.EvpError):
+        evp_lib.ternary_knn(Vs[:1], Vs, 64, 10, 9, path=3)     # unknown path
+    many = torch.zeros((300, 2), dtype=torch.int64, device=dev)
+    with pytest.raises(evp_lib.EvpError):
+        evp_lib.ternary_knn(many[:20], many, 64, 10, 129, path=2)   # k above the MMA limit
     ws = torch.empty(256, dtype=torch.uint8, device=dev)
     out = torch.empty(16, dtype=torch.int64, device=dev)
     rc = evp_lib.load().ternary_knn(Vs.data_ptr(), 1, Vs.data_ptr(), 10, 64, 10, 3,

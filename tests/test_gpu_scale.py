@@ -28,14 +28,14 @@ def db_1m(dev):
     return U, Q, U.cpu().numpy(), Q.cpu().numpy()
 
 
-@pytest.mark.parametrize("x", [64, 256, 384])
-def test_scale_1m_exhaustive_queries(evp_lib, dev, db_1m, x):
+@pytest.mark.parametrize("x,path", [(64, 1), (256, 1), (384, 1), (256, 2), (64, 2)])
+def test_scale_1m_exhaustive_queries(evp_lib, dev, db_1m, x, path):
     U, Q, U_h, Q_h = db_1m
     d, k = 768, 100
     st = evp_lib.new_status(dev)
     Ts = evp_lib.encode(U, x, status=st)
     Tq = evp_lib.encode(Q, x, status=st)
-    ids, dist = evp_lib.ternary_knn(Tq, Ts, d, x, k, status=st)
+    ids, dist = evp_lib.ternary_knn(Tq, Ts, d, x, k, status=st, path=path)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     Vs = par_encode(U_h, x)
