@@ -139,6 +139,31 @@ int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns
                     int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist,
                     void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
 
+/* ---------------------------------------------------------------------
+ * ternary_knn_static -- ternary_knn (popcount path) that allocates
+ * nothing.  The paper has no counterpart; this exists for callers that
+ * cannot allocate device memory: code running inside a CUDA graph capture
+ * (where cudaMalloc is not allowed), serving threads that must never enter
+ * the device allocator, plugins handed raw device pointers by a host that
+ * owns all allocation, and plain C callers with no allocator.  Inputs and
+ * outputs are the caller's, as in ternary_knn; the workspace is a fixed
+ * EVP_STATIC_SCRATCH_BYTES (16 MiB) array inside the library, present on
+ * every GPU that loads it.  A request whose popcount-path workspace
+ * (ternary_knn_path_workspace(nq, ns, d, k, EVP_PATH_POPC)) exceeds that
+ * size is rejected with EVP_ERR_NO_MEMORY before anything is launched.
+ * The first call on each device looks up the array's device address (with
+ * that device current) and caches it, so make that first call before any
+ * stream capture that includes this entry point.  All calls share the one
+ * array and it keeps the previous call's contents (each call re-initialises
+ * what it reads): calls that overlap on the GPU race on it, so the caller
+ * must order them (one stream, or events).  Results are identical to
+ * ternary_knn with EVP_PATH_POPC.
+ * ------------------------------------------------------------------- */
+#define EVP_STATIC_SCRATCH_BYTES (16u << 20)
+int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns,
+                           int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist,
+                           int32_t* dev_status, void* stream);
+
 /* Scan paths.  Both return identical results.
  *   EVP_PATH_POPC  bitplane popcount scan on the integer pipe: reads the
  *                  packed codes once per 16 queries; best for small batches.

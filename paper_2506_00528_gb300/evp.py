@@ -52,6 +52,7 @@ SIGNATURES = {
     "ternary_knn_path_workspace": (_sz, [_i64, _i64, _i32, _i32, _i32]),
     "ternary_knn_path": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _sz, _p, _p,
                                 _i32]),
+    "ternary_knn_static": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
     "rerank": (_i32, [_p, _i64, _p, _i64, _i32, _p, _i32, _i32, _p, _p, _p, _p]),
     "evp_db_create": (_i32, [_p, _p, _i64, _i32, _i32, _i32, _p, ctypes.POINTER(_p)]),
     "evp_db_destroy": (_i32, [_p]),
@@ -187,6 +188,20 @@ def ternary_knn(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
                                      _ptr(ids), _ptr(dist), _ptr(ws), ws.numel(), _ptr(status),
                                      _stream_handle(stream), int(path))
     _check(rc, "ternary_knn")
+    return ids, dist
+
+
+def ternary_knn_static(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
+                       ids: torch.Tensor, dist: torch.Tensor, status: torch.Tensor | None = None,
+                       stream=None):
+    """ternary_knn_static: the popcount scan with the library's fixed scratch
+    (no allocation by the library; outputs must be given)."""
+    _req(Q, torch.int64, "Q")
+    _req(S, torch.int64, "S")
+    rc = load().ternary_knn_static(_ptr(Q), Q.shape[0], _ptr(S), S.shape[0], int(d), int(x),
+                                   int(k), _ptr(ids), _ptr(dist), _ptr(status),
+                                   _stream_handle(stream))
+    _check(rc, "ternary_knn_static")
     return ids, dist
 
 
