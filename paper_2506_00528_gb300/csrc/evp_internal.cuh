@@ -185,7 +185,7 @@ struct MmaPlan {
     int qtiles;             // 128-query tiles
     int nslices;            // database slices per query tile
     int64_t rows_per_slice;
-    size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, ws_bytes;
+    size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, hist_bytes, ws_bytes;
 };
 constexpr int MMA_K_MAX = 128;  // largest k of the tensor-core path
 int mma_kp(int d);

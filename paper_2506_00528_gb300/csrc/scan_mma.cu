@@ -23,8 +23,10 @@
 //               (Delta/2 << 20 | row-in-slice) keys in shared memory.  A row
 //               is a candidate only if its D beats the heap root (rows arrive
 //               in ascending index order, so an equal Delta never displaces)
-//               and is not worse than the best k-th Delta any other slice of
-//               the same query has published (atomicMin in the workspace).
+//               and is not worse than the union bound: every key any slice
+//               of the query inserts is counted in a per-query Delta
+//               histogram in the workspace, and the k-th smallest counted
+//               Delta bounds the answer for all slices.
 //               Each 32-column TMEM load is first reduced to its maximum, so
 //               a warp skips the group when no lane has a candidate;
 //               candidates go to a small per-thread staging buffer, and the
@@ -54,7 +56,7 @@ constexpr int A_STAGE_BYTES = MMA_M * KCHUNK;
 constexpr int B_STAGE_BYTES = MMA_N * KCHUNK;
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
 constexpr int HEAP_BYTES = HEAP_K_MAX * MMA_M * 4;
-constexpr int STAGE_SLOTS = 16;                     // per-thread candidate staging
+constexpr int STAGE_SLOTS = 32;                     // per-thread candidate staging
 constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
@@ -76,7 +78,10 @@ struct MmaArgs {
     int64_t rows_per_slice;
     uint64_t* lists;       // [nq][nslices][2][k], buffer 0 used
     int32_t* meta;         // [nq][nslices][2]
-    uint64_t* tau_global;  // [nq]
+    uint64_t* tau_global;  // [nq] (unused by the tensor path)
+    uint32_t* hist;        // [nq][hist_bins]: Delta/2 of every key any slice inserted
+    uint32_t* minhalf;     // [nq]: smallest Delta/2 any slice inserted
+    int hist_bins;         // 2x + 1
     int32_t* status;
 };
 
@@ -294,31 +299,67 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int64_t qrow = (int64_t)qt * MMA_M + m;
         const bool valid_q = qrow < a.nq;
         const int k = a.k;
-        uint32_t* tau_half = reinterpret_cast<uint32_t*>(a.tau_global);
+        uint32_t* hist = a.hist + (valid_q ? qrow : 0) * (int64_t)a.hist_bins;
         int hs = 0;
         float dtau = -INFINITY;   // own heap root: accept D > dtau (strict: rows arrive in order)
-        float dglob = -INFINITY;  // best k-th Delta/2 any slice has published: accept D >= it
-        uint32_t published = 0xFFFFFFFFu;
+        float dglob = -INFINITY;  // union bound: accept D >= x - uthr
+        uint32_t uthr = 0xFFFFFFFFu;     // k-th smallest Delta/2 over all slices' inserted keys
+        uint32_t lmin = 0xFFFFFFFFu;     // smallest Delta/2 this thread inserted
         int sc = 0;  // staged candidates of this thread
         // Insert the staged candidates into the heap.  All lanes of the warp
         // flush together, so their heap updates run side by side instead of
-        // one lane at a time.
+        // one lane at a time.  Every inserted key is also counted in the
+        // query's Delta/2 histogram shared by all slices.
         auto flush = [&]() {
             const int cmax = __reduce_max_sync(0xffffffffu, sc);
+            const uint32_t old_min = lmin;
             for (int i = 0; i < cmax; ++i) {
                 if (i < sc) {
                     const uint32_t key = staging[i * MMA_M + m];
+                    bool ins = false;
                     if (hs < k) {
                         heap_push(heap, m, hs, key);
                         ++hs;
+                        ins = true;
                     } else if (key < heap[m]) {
                         heap[m] = key;
                         heap_sift_down(heap, m, hs, 0);
+                        ins = true;
+                    }
+                    if (ins) {
+                        const uint32_t h = key >> LOCAL_BITS;
+                        atomicAdd(&hist[h], 1u);
+                        lmin = min(lmin, h);
                     }
                 }
             }
+            if (lmin < old_min) atomicMin(&a.minhalf[qrow], lmin);
             sc = 0;
             if (hs == k) dtau = (float)(a.x - (int)(heap[m] >> LOCAL_BITS));
+        };
+        // Union bound: the smallest T with count(Delta/2 <= T) >= k over the
+        // keys all slices of this query have inserted.  Those are real rows,
+        // so no row with Delta/2 > T can be among the k nearest.
+        auto refresh_union = [&]() {
+            const uint32_t lo = *reinterpret_cast<volatile uint32_t*>(&a.minhalf[qrow]);
+            if (lo == 0xFFFFFFFFu) return;
+            const uint32_t hi = min(uthr, (uint32_t)(a.hist_bins - 1));
+            uint32_t cum = 0;
+            for (uint32_t h0 = lo; h0 <= hi; h0 += 8) {
+                uint32_t c8[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    c8[u] = (h0 + u <= hi) ? *reinterpret_cast<volatile uint32_t*>(&hist[h0 + u]) : 0u;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    cum += c8[u];
+                    if (cum >= (uint32_t)k && h0 + u < uthr) {
+                        uthr = h0 + u;
+                        dglob = (float)(a.x - (int)uthr) - 0.5f;
+                        return;
+                    }
+                }
+            }
         };
         bool ok = true;
         for (int t = 0; t < ntiles; ++t) {
@@ -334,10 +375,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 break;
             }
             tc_fence_after();
-            if (valid_q) {
-                const uint32_t g = *reinterpret_cast<volatile uint32_t*>(&tau_half[qrow]);
-                if (g != 0xFFFFFFFFu) dglob = (float)(a.x - (int)g) - 0.5f;
-            }
+            if (valid_q && (t & 3) == 1) refresh_union();
             const int64_t tile_row = row0 + (int64_t)t * MMA_N;
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * MMA_N);
             for (int c = 0; c < MMA_N / 32; ++c) {
@@ -347,34 +385,28 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 float mx = __uint_as_float(v[0]);
 #pragma unroll
                 for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(v[j]));
-                float thr = fmaxf(dtau, dglob);
+                const float thr = fmaxf(dtau, dglob);
                 if (!__any_sync(0xffffffffu, valid_q && mx > thr)) continue;
+                uint32_t cm = 0;
 #pragma unroll
-                for (int jc = 0; jc < 4; ++jc) {
+                for (int j = 0; j < 32; ++j) cm |= (__uint_as_float(v[j]) > thr ? 1u : 0u) << j;
+                const int64_t left = row_end - (tile_row + c * 32);  // rows of this group in range
+                if (!valid_q || left <= 0) cm = 0;
+                else if (left < 32) cm &= (1u << left) - 1u;
+                const uint32_t gbase = (uint32_t)(tile_row + c * 32 - row0);
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float dot = __uint_as_float(v[jc * 8 + j]);
-                        const int64_t row = tile_row + c * 32 + jc * 8 + j;
-                        if (valid_q && dot > thr && row < row_end) {
-                            const uint32_t half_delta = (uint32_t)(a.x - __float2int_rn(dot));
+                for (int jc = 0; jc < 2; ++jc) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        if ((cm >> (jc * 16 + j)) & 1u) {
+                            const uint32_t half_delta =
+                                (uint32_t)(a.x - __float2int_rn(__uint_as_float(v[jc * 16 + j])));
                             staging[sc * MMA_M + m] =
-                                (half_delta << LOCAL_BITS) | (uint32_t)(row - row0);
+                                (half_delta << LOCAL_BITS) | (gbase + (uint32_t)(jc * 16 + j));
                             ++sc;
                         }
                     }
-                    if (__any_sync(0xffffffffu, sc > STAGE_SLOTS - 8)) {
-                        flush();
-                        thr = fmaxf(dtau, dglob);
-                    }
-                }
-            }
-            if (hs == k && valid_q) {
-                // share this slice's k-th Delta/2: no row with a larger Delta anywhere
-                // can be among the query's k nearest
-                const uint32_t root_half = heap[m] >> LOCAL_BITS;
-                if (root_half < published) {
-                    atomicMin(&tau_half[qrow], root_half);
-                    published = root_half;
+                    if (__any_sync(0xffffffffu, sc > STAGE_SLOTS - 16)) flush();
                 }
             }
             tc_fence_before();
@@ -448,9 +480,15 @@ __global__ void unpack_fp8_kernel(const uint64_t* __restrict__ T, int64_t n, int
     reinterpret_cast<uint4*>(out + row * (int64_t)Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
-__global__ void init_tau_n_kernel(uint64_t* tau, int n) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) tau[i] = KEY_NONE;
+__global__ void init_tau_n_kernel(uint64_t* tau, int n, uint32_t* hist, int64_t hist_words,
+                                  uint32_t* minhalf) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0; i < n; i += stride) {
+        tau[i] = KEY_NONE;
+        minhalf[i] = 0xFFFFFFFFu;
+    }
+    for (int64_t i = i0; i < hist_words; i += stride) hist[i] = 0u;
 }
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
@@ -476,7 +514,8 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
     p.list_bytes = align256((size_t)nq * p.nslices * 2 * k * 8);
     p.meta_bytes = align256((size_t)nq * p.nslices * 2 * 4);
     p.tau_bytes = align256((size_t)nq * 8);
-    p.ws_bytes = p.a_bytes + p.b_bytes + p.list_bytes + p.meta_bytes + p.tau_bytes;
+    p.hist_bytes = align256((size_t)nq * (2 * d + 1) * 4) + align256((size_t)nq * 4);
+    p.ws_bytes = p.a_bytes + p.b_bytes + p.list_bytes + p.meta_bytes + p.tau_bytes + p.hist_bytes;
     return p;
 }
 
@@ -503,13 +542,20 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     int32_t* meta = reinterpret_cast<int32_t*>(w + p.a_bytes + p.b_bytes + p.list_bytes);
     uint64_t* tau = reinterpret_cast<uint64_t*>(w + p.a_bytes + p.b_bytes + p.list_bytes +
                                                 p.meta_bytes);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(tau) + p.tau_bytes);
+    const int hist_bins = 2 * x + 1;
+    uint32_t* minhalf = reinterpret_cast<uint32_t*>(
+        reinterpret_cast<uint8_t*>(hist) + align256((size_t)nq * (2 * d + 1) * 4));
     if ((reinterpret_cast<uintptr_t>(B8) & 255) != 0) return EVP_ERR_INVALID;
 
     if (launch_unpack_fp8(Q, nq, d, A8, stream) != cudaSuccess) return EVP_ERR_CUDA;
     if (!S8 && launch_unpack_fp8(S, ns, d, B8, stream) != cudaSuccess) return EVP_ERR_CUDA;
     {
         TimedLaunch timer("scan_init", stream);
-        init_tau_n_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, stream>>>(tau, (int)nq);
+        const int64_t hw = nq * (int64_t)hist_bins;
+        const int64_t blocks = std::min<int64_t>((hw + 255) / 256, (int64_t)num_sms() * 8);
+        init_tau_n_kernel<<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, stream>>>(
+            tau, (int)nq, hist, hw, minhalf);
     }
 
     EncodeTiledFn enc = encode_tiled_fn();
@@ -540,6 +586,9 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.lists = lists;
     args.meta = meta;
     args.tau_global = tau;
+    args.hist = hist;
+    args.minhalf = minhalf;
+    args.hist_bins = hist_bins;
     args.status = status;
     if (cudaFuncSetAttribute(scan_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES) != cudaSuccess)

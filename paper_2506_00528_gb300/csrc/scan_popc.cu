@@ -94,9 +94,15 @@ __device__ inline int next_pow2(int v) {
     return p;
 }
 
-template <int QB>
-__global__ void __launch_bounds__(SCAN_ROWS, 1)
+// TPR threads share a row (each takes QB / TPR of the pass's queries), so a
+// CTA runs SCAN_ROWS * TPR threads: more warps to hide the popcount and
+// shared-memory latencies than one thread per row would give.
+template <int QB, int TPR>
+__global__ void __launch_bounds__(SCAN_ROWS * TPR, 1)
 scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
+    constexpr int NT = SCAN_ROWS * TPR;
+    constexpr int QPT = QB / TPR;
+    static_assert(QPT * TPR == QB, "queries split evenly over a row's threads");
     extern __shared__ __align__(1024) uint8_t smem[];
     const SmemLayout L = smem_layout(a.W, a.stages, QB);
     uint64_t* qv = reinterpret_cast<uint64_t*>(smem + L.qv_off);
@@ -109,6 +115,8 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
     int* abort_flag = reinterpret_cast<int*>(smem + L.flag_off);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rt = tid % SCAN_ROWS;          // row of the tile this thread scores
+    const int qbase = (tid / SCAN_ROWS) * QPT;  // first query of this thread
     const int W = a.W, k = a.k, nslices = gridDim.x, slice = blockIdx.x;
     const int64_t tile0 = (int64_t)slice * a.tiles_per_slice;
     const int64_t tile_end = min(tile0 + a.tiles_per_slice, a.ntiles);
@@ -120,7 +128,7 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         fence_mbar_init();
         *abort_flag = 0;
     }
-    for (int i = tid; i < QB * W; i += SCAN_ROWS) {
+    for (int i = tid; i < QB * W; i += NT) {
         const int q = i / W, w = i - q * W;
         uint64_t p = 0, n = 0;
         if (q < a.nqg) {
@@ -157,33 +165,34 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         __syncthreads();
         if (*abort_flag) break;
 
-        const int64_t row = (tile0 + it) * SCAN_ROWS + tid;
+        const int64_t row = (tile0 + it) * SCAN_ROWS + rt;
         if (row < a.ns) {
             const uint64_t* rp =
-                reinterpret_cast<const uint64_t*>(smem + s * L.stage_bytes) + tid * a.pitch;
-            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qv);
-            int acc_one[QB], acc_opp[QB];
+                reinterpret_cast<const uint64_t*>(smem + s * L.stage_bytes) + rt * a.pitch;
+            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qv) + qbase * W;
+            int acc_one[QPT], acc_opp[QPT];
 #pragma unroll
-            for (int q = 0; q < QB; ++q) acc_one[q] = acc_opp[q] = 0;
+            for (int q = 0; q < QPT; ++q) acc_one[q] = acc_opp[q] = 0;
 #pragma unroll 2
             for (int w = 0; w < W; ++w) {
                 const uint64_t sp = rp[w], sn = rp[W + w];
                 const uint64_t sm = sp | sn;
 #pragma unroll
-                for (int q = 0; q < QB; ++q) {
+                for (int q = 0; q < QPT; ++q) {
                     const ulonglong2 qq = q2[q * W + w];
                     acc_one[q] += __popcll(qq.x ^ sm);
                     acc_opp[q] += __popcll(qq.x & sm & (qq.y ^ sn));
                 }
             }
 #pragma unroll
-            for (int q = 0; q < QB; ++q) {
-                if (q < a.nqg) {
+            for (int q = 0; q < QPT; ++q) {
+                const int gq = qbase + q;
+                if (gq < a.nqg) {
                     const uint32_t delta = (uint32_t)(acc_one[q] + 4 * acc_opp[q]);
                     const uint64_t key = ((uint64_t)delta << 32) | (uint64_t)row;
-                    if (key < tau[q]) {
-                        const int pos = atomicAdd(&cnt[q], 1);
-                        cand[q * CAND_CAP + pos] = key;
+                    if (key < tau[gq]) {
+                        const int pos = atomicAdd(&cnt[gq], 1);
+                        cand[gq * CAND_CAP + pos] = key;
                     }
                 }
             }
@@ -204,7 +213,7 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         }
         if (mask) {
             __syncthreads();  // every thread has read cnt before it changes
-            for (int q = warp; q < QB; q += SCAN_ROWS / 32) {
+            for (int q = warp; q < QB; q += NT / 32) {
                 if (!((mask >> q) & 1)) continue;
                 uint64_t* C = cand + q * CAND_CAP;
                 const int nc = cnt[q];
@@ -373,15 +382,15 @@ int choose_stages(int W, int qb) {
     return 0;
 }
 
-template <int QB>
+template <int QB, int TPR>
 cudaError_t launch_scan(const CUtensorMap& tmap, const ScanArgs& a, int nslices, size_t smem,
                         cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<QB>,
+    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<QB, TPR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SMEM_BUDGET + 2048);
     if (e != cudaSuccess) return e;
     TimedLaunch timer("scan_popc", stream);
-    scan_popc_kernel<QB><<<nslices, SCAN_ROWS, smem, stream>>>(tmap, a);
+    scan_popc_kernel<QB, TPR><<<nslices, SCAN_ROWS * TPR, smem, stream>>>(tmap, a);
     return cudaGetLastError();
 }
 
@@ -471,11 +480,11 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
             init_tau_kernel<<<1, 32, 0, stream>>>(a.tau_global);
         }
         cudaError_t e;
-        if (nqg <= 1) e = launch_scan<1>(tmap, a, p.nslices, L.total, stream);
-        else if (nqg <= 2) e = launch_scan<2>(tmap, a, p.nslices, L.total, stream);
-        else if (nqg <= 4) e = launch_scan<4>(tmap, a, p.nslices, L.total, stream);
-        else if (nqg <= 8) e = launch_scan<8>(tmap, a, p.nslices, L.total, stream);
-        else e = launch_scan<16>(tmap, a, p.nslices, L.total, stream);
+        if (nqg <= 1) e = launch_scan<1, 1>(tmap, a, p.nslices, L.total, stream);
+        else if (nqg <= 2) e = launch_scan<2, 2>(tmap, a, p.nslices, L.total, stream);
+        else if (nqg <= 4) e = launch_scan<4, 2>(tmap, a, p.nslices, L.total, stream);
+        else if (nqg <= 8) e = launch_scan<8, 2>(tmap, a, p.nslices, L.total, stream);
+        else e = launch_scan<16, 2>(tmap, a, p.nslices, L.total, stream);
         if (e != cudaSuccess) return EVP_ERR_CUDA;
         const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, nqg, p.nslices, k,
                                               ids + q0 * k, dist + q0 * k, stream);
