@@ -258,6 +258,7 @@ int32_t evp_db_create(const uint64_t* T, const float* U, int64_t ns, int32_t d, 
 int32_t evp_db_destroy(evp_db_t db);
 int32_t evp_db_dim(evp_db_t db);   /* d of the database (0 for NULL) */
 int64_t evp_db_rows(evp_db_t db);  /* ns of the database (0 for NULL) */
+const uint64_t* evp_db_codes(evp_db_t db);  /* the borrowed packed codes T */
 size_t evp_db_knn_workspace(evp_db_t db, int64_t nq, int32_t k, int32_t path);
 int32_t evp_db_knn(evp_db_t db, const uint64_t* Q, int64_t nq, int32_t k, int64_t* ids,
                    int32_t* dist, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream,
@@ -266,10 +267,69 @@ size_t evp_db_search_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int
 int32_t evp_db_search(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortlist, int32_t k,
                       int64_t* ids, float* scores, void* ws, size_t ws_bytes,
                       int32_t* dev_status, void* stream);
+/* evp_db_search with the scan path forced (EVP_PATH_*); same results. */
+size_t evp_db_search_path_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k,
+                                    int32_t path);
+int32_t evp_db_search_path(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortlist,
+                           int32_t k, int64_t* ids, float* scores, void* ws, size_t ws_bytes,
+                           int32_t* dev_status, void* stream, int32_t path);
 size_t evp_db_search_host_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k);
 int32_t evp_db_search_host(evp_db_t db, const float* Q_host, int64_t nq, int32_t n_shortlist,
                            int32_t k, int64_t* ids_host, float* scores_host, void* ws,
                            size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Batched form: many query batches of uneven sizes against several
+ * resident databases, planned once and replayed (no counterpart in the
+ * paper; it batches the Sec. 5.3 search).
+ *
+ * An evp_batch_desc is either a whole-path search (Q = float32 queries
+ * [nq][d] on the device, n_shortlist >= k, outputs ids and scores, as
+ * evp_db_search) or a plain kNN (Q = NULL, Qc = packed codes [nq][2W],
+ * outputs ids and dist, as evp_db_knn).  All pointers are device pointers
+ * owned by the caller and must stay valid while the plan exists.
+ *
+ * evp_autotune times the popcount and tensor-core scans on a database for
+ * a query count (rounded up to a power of two) and k, using the database's
+ * own rows as trial queries, and caches the faster path per (database,
+ * query-count bucket, k); *path_out receives it, and *popc_ms / *mma_ms
+ * (optional) the timings, which force a fresh measurement when requested.
+ * It allocates temporary device memory.
+ *
+ * evp_batch_plan_create checks every descriptor, picks each batch's path
+ * with evp_autotune (EVP_BATCH_NO_TUNE: the automatic rule instead), and
+ * allocates one workspace region per batch (the plan owns it).
+ * evp_batch_run enqueues all batches on `stream`, dealing them over four
+ * forked streams that join back into `stream`; with EVP_BATCH_GRAPH the
+ * first run captures this into a CUDA graph (`stream` must not be the
+ * legacy default stream) and every run launches the graph.  Results equal
+ * the per-batch evp_db_search / evp_db_knn calls.  dev_status is shared by
+ * all batches (and baked into the graph at capture).
+ * ------------------------------------------------------------------- */
+typedef struct {
+    evp_db_t db;
+    const float* Q;       /* float32 queries [nq][d], or NULL for a plain kNN */
+    const uint64_t* Qc;   /* packed query codes [nq][2W] (plain kNN)          */
+    int64_t nq;
+    int32_t n_shortlist;  /* search: shortlist length by Delta (>= k)         */
+    int32_t k;
+    int64_t* ids;         /* [nq][k]                                          */
+    float* scores;        /* search: [nq][k]                                  */
+    int32_t* dist;        /* plain kNN: [nq][k] Delta                         */
+} evp_batch_desc;
+typedef struct evp_batch_plan* evp_batch_plan_t;
+#define EVP_BATCH_GRAPH   1
+#define EVP_BATCH_NO_TUNE 2
+
+int32_t evp_autotune(evp_db_t db, int64_t nq, int32_t k, int32_t* path_out, float* popc_ms,
+                     float* mma_ms, void* stream);
+int32_t evp_autotune_clear(void);
+int32_t evp_batch_plan_create(const evp_batch_desc* batches, int32_t nb, int32_t flags,
+                              void* stream, evp_batch_plan_t* out);
+int32_t evp_batch_plan_path(evp_batch_plan_t plan, int32_t i);   /* chosen path of batch i */
+size_t evp_batch_plan_workspace(evp_batch_plan_t plan);
+int32_t evp_batch_run(evp_batch_plan_t plan, int32_t* dev_status, void* stream);
+int32_t evp_batch_plan_destroy(evp_batch_plan_t plan);
 
 /* ---------------------------------------------------------------------
  * Serving: a continuous-batching request loop over a resident database

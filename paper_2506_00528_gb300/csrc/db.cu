@@ -35,12 +35,13 @@ struct SearchLayout {
     size_t codes, sl_ids, sl_dist, knn, total;
 };
 
-SearchLayout search_layout(const evp_db* db, int64_t nq, int32_t n_shortlist) {
+SearchLayout search_layout(const evp_db* db, int64_t nq, int32_t n_shortlist,
+                           int32_t path = EVP_PATH_AUTO) {
     SearchLayout L;
     L.codes = align256((size_t)nq * 2 * db->W * 8);
     L.sl_ids = align256((size_t)nq * n_shortlist * 8);
     L.sl_dist = align256((size_t)nq * n_shortlist * 4);
-    L.knn = align256(db_knn_ws(db, nq, n_shortlist, EVP_PATH_AUTO));
+    L.knn = align256(db_knn_ws(db, nq, n_shortlist, path));
     L.total = L.codes + L.sl_ids + L.sl_dist + L.knn;
     return L;
 }
@@ -92,6 +93,8 @@ int32_t evp_db_dim(evp_db_t db) { return db ? db->d : 0; }
 
 int64_t evp_db_rows(evp_db_t db) { return db ? db->ns : 0; }
 
+const uint64_t* evp_db_codes(evp_db_t db) { return db ? db->T : nullptr; }
+
 int32_t evp_db_destroy(evp_db_t db) {
     if (!db) return EVP_ERR_INVALID;
     int32_t rc = EVP_OK;
@@ -125,21 +128,28 @@ int32_t evp_db_knn(evp_db_t db, const uint64_t* Q, int64_t nq, int32_t k, int64_
                         dev_status, s);
 }
 
-size_t evp_db_search_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k) {
+size_t evp_db_search_path_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k,
+                                    int32_t path) {
     if (!db || nq <= 0 || n_shortlist < 1 || k < 1) return 0;
-    return search_layout(db, nq, n_shortlist).total;
+    return search_layout(db, nq, n_shortlist, path).total;
 }
 
-int32_t evp_db_search(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortlist, int32_t k,
-                      int64_t* ids, float* scores, void* ws, size_t ws_bytes, int32_t* dev_status,
-                      void* stream) {
+size_t evp_db_search_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k) {
+    return evp_db_search_path_workspace(db, nq, n_shortlist, k, EVP_PATH_AUTO);
+}
+
+int32_t evp_db_search_path(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortlist,
+                           int32_t k, int64_t* ids, float* scores, void* ws, size_t ws_bytes,
+                           int32_t* dev_status, void* stream, int32_t path) {
     if (!db) return EVP_ERR_INVALID;
-    if (nq < 0 || k < 1 || n_shortlist < k || (int64_t)n_shortlist > db->ns) return EVP_ERR_INVALID;
+    if (nq < 0 || k < 1 || n_shortlist < k || (int64_t)n_shortlist > db->ns ||
+        path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
+        return EVP_ERR_INVALID;
     if (n_shortlist > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
     if (nq == 0) return EVP_OK;
     if (!db->U || !Q || !ids || !scores || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
         return EVP_ERR_INVALID;
-    const SearchLayout L = search_layout(db, nq, n_shortlist);
+    const SearchLayout L = search_layout(db, nq, n_shortlist, path);
     if (ws_bytes < L.total) return EVP_ERR_NO_MEMORY;
     uint8_t* w = static_cast<uint8_t*>(ws);
     uint64_t* codes = reinterpret_cast<uint64_t*>(w);
@@ -150,12 +160,19 @@ int32_t evp_db_search(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortli
     if (launch_encode(Q, nq, db->d, db->x, codes, dev_status, s) != cudaSuccess)
         return EVP_ERR_CUDA;
     const int32_t rc = evp_db_knn(db, codes, nq, n_shortlist, sl_ids, sl_dist, knn_ws, L.knn,
-                                  dev_status, stream, EVP_PATH_AUTO);
+                                  dev_status, stream, path);
     if (rc != EVP_OK) return rc;
     if (launch_rerank(Q, nq, db->U, db->ns, db->d, sl_ids, n_shortlist, k, ids, scores,
                       dev_status, s) != cudaSuccess)
         return EVP_ERR_CUDA;
     return EVP_OK;
+}
+
+int32_t evp_db_search(evp_db_t db, const float* Q, int64_t nq, int32_t n_shortlist, int32_t k,
+                      int64_t* ids, float* scores, void* ws, size_t ws_bytes, int32_t* dev_status,
+                      void* stream) {
+    return evp_db_search_path(db, Q, nq, n_shortlist, k, ids, scores, ws, ws_bytes, dev_status,
+                              stream, EVP_PATH_AUTO);
 }
 
 size_t evp_db_search_host_workspace(evp_db_t db, int64_t nq, int32_t n_shortlist, int32_t k) {

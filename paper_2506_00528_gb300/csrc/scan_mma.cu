@@ -76,6 +76,7 @@ struct MmaArgs {
     int x;
     int k;
     int64_t rows_per_slice;
+    int qtiles, nslices;   // work items = qtiles * nslices
     uint64_t* lists;       // [nq][nslices][2][k], buffer 0 used
     int32_t* meta;         // [nq][nslices][2]
     uint64_t* tau_global;  // [nq] (unused by the tensor path)
@@ -192,11 +193,25 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int qt = blockIdx.y, slice = blockIdx.x, nslices = gridDim.x;
-    const int64_t row0 = (int64_t)slice * a.rows_per_slice;
-    const int64_t row_end = min(row0 + a.rows_per_slice, a.ns);
-    const int ntiles = row_end > row0 ? (int)((row_end - row0 + MMA_N - 1) / MMA_N) : 0;
+    const int nslices = a.nslices;
+    const int nitems = a.qtiles * a.nslices;
     const int kchunks = a.kchunks;
+    // Work item -> (query tile, database slice).  Consecutive items share a
+    // slice, so the CTAs of one wave that work on the same slice read its
+    // rows from L2 rather than HBM.
+    struct Item {
+        int qt, slice, ntiles;
+        int64_t row0, row_end;
+    };
+    auto item_of = [&](int item) {
+        Item w;
+        w.qt = item % a.qtiles;
+        w.slice = item / a.qtiles;
+        w.row0 = (int64_t)w.slice * a.rows_per_slice;
+        w.row_end = min(w.row0 + a.rows_per_slice, a.ns);
+        w.ntiles = w.row_end > w.row0 ? (int)((w.row_end - w.row0 + MMA_N - 1) / MMA_N) : 0;
+        return w;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -228,19 +243,22 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // ---------------- TMA producer ----------------
             int it = 0;
             bool ok = true;
-            for (int t = 0; t < ntiles && ok; ++t) {
-                for (int kc = 0; kc < kchunks; ++kc, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                    if (!mbar_wait_bounded(&empty[s], ph ^ 1u) || *(volatile int*)abort_flag) {
-                        ok = false;
-                        break;
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+                const Item w = item_of(item);
+                for (int t = 0; t < w.ntiles && ok; ++t) {
+                    for (int kc = 0; kc < kchunks; ++kc, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                        if (!mbar_wait_bounded(&empty[s], ph ^ 1u) || *(volatile int*)abort_flag) {
+                            ok = false;
+                            break;
+                        }
+                        uint8_t* st = stages + s * STAGE_BYTES;
+                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                        tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, w.qt * MMA_M);
+                        tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK,
+                                    (int32_t)(w.row0 + (int64_t)t * MMA_N));
                     }
-                    uint8_t* st = stages + s * STAGE_BYTES;
-                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, qt * MMA_M);
-                    tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK,
-                                (int32_t)(row0 + (int64_t)t * MMA_N));
                 }
             }
             if (!ok) {
@@ -254,11 +272,13 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            int it = 0;
+            int it = 0, tt = 0;
             bool ok = true;
-            for (int t = 0; t < ntiles && ok; ++t) {
-                const int b = t & 1;
-                const uint32_t use = (uint32_t)(t >> 1);
+            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+              const Item w = item_of(item);
+              for (int t = 0; t < w.ntiles && ok; ++t, ++tt) {
+                const int b = tt & 1;
+                const uint32_t use = (uint32_t)(tt >> 1);
                 if (!mbar_wait_bounded(&acc_empty[b], (use & 1u) ^ 1u)) {
                     ok = false;
                     break;
@@ -283,6 +303,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     mma_commit(&empty[s]);
                 }
                 if (ok) mma_commit(&acc_full[b]);
+              }
             }
             if (!ok) {
                 report(a.status, EVP_ERR_TIMEOUT);
@@ -296,9 +317,15 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
         const int m = quarter * 32 + lane;  // TMEM lane = query row in the tile
-        const int64_t qrow = (int64_t)qt * MMA_M + m;
-        const bool valid_q = qrow < a.nq;
         const int k = a.k;
+        int tt = 0;  // accumulator tiles consumed so far (all items)
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        const Item w = item_of(item);
+        const int slice = w.slice, ntiles = w.ntiles;
+        const int64_t row0 = w.row0, row_end = w.row_end;
+        const int64_t qrow = (int64_t)w.qt * MMA_M + m;
+        const bool valid_q = qrow < a.nq;
         uint32_t* hist = a.hist + (valid_q ? qrow : 0) * (int64_t)a.hist_bins;
         int hs = 0;
         float dtau = -INFINITY;   // own heap root: accept D > dtau (strict: rows arrive in order)
@@ -361,10 +388,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 }
             }
         };
-        bool ok = true;
-        for (int t = 0; t < ntiles; ++t) {
-            const int b = t & 1;
-            const uint32_t use = (uint32_t)(t >> 1);
+        for (int t = 0; t < ntiles; ++t, ++tt) {
+            const int b = tt & 1;
+            const uint32_t use = (uint32_t)(tt >> 1);
             // one lane waits, the warp follows it (keeps the warp converged)
             int got = 1;
             if (lane == 0)
@@ -412,11 +438,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             tc_fence_before();
             mbar_arrive(&acc_empty[b]);
         }
-        if (ok) flush();
-        if (!ok) {
-            report(a.status, EVP_ERR_TIMEOUT);
-            *(volatile int*)abort_flag = 1;
-        } else if (valid_q) {
+        if (!ok) break;
+        flush();
+        if (valid_q) {
             // heap -> ascending order in place, then the (query, slice) list
             for (int n = hs - 1; n > 0; --n) {
                 const uint32_t top = heap[m];
@@ -438,6 +462,11 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             if (hs == k)
                 atomicMin(reinterpret_cast<unsigned long long*>(&a.tau_global[qrow]),
                           (unsigned long long)last);
+        }
+        }  // item
+        if (!ok) {
+            report(a.status, EVP_ERR_TIMEOUT);
+            *(volatile int*)abort_flag = 1;
         }
     }
 
@@ -503,8 +532,18 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
     p.qtiles = (int)((nq + MMA_M - 1) / MMA_M);
     const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
     const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
-    int64_t slices = std::max<int64_t>(1, num_sms() / std::max(1, p.qtiles));
-    slices = std::max(slices, min_slices);
+    // qtiles * slices a multiple of the SM count (whole waves of the
+    // persistent grid), at least min_slices, at most one slice per tile
+    const int64_t sms = num_sms();
+    int64_t g = sms, b = std::max(1, p.qtiles);
+    while (b) {
+        const int64_t r = g % b;
+        g = b;
+        b = r;
+    }
+    const int64_t step = sms / g;
+    int64_t slices = step;
+    while (slices < min_slices) slices += step;
     slices = std::min(slices, std::max<int64_t>(1, ntiles));
     const int64_t tiles_per_slice = (ntiles + slices - 1) / slices;
     p.rows_per_slice = tiles_per_slice * MMA_N;
@@ -583,6 +622,8 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.x = x;
     args.k = k;
     args.rows_per_slice = p.rows_per_slice;
+    args.qtiles = p.qtiles;
+    args.nslices = p.nslices;
     args.lists = lists;
     args.meta = meta;
     args.tau_global = tau;
@@ -595,8 +636,9 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
         return EVP_ERR_CUDA;
     {
         TimedLaunch timer("scan_mma", stream);
-        scan_mma_kernel<<<dim3(p.nslices, p.qtiles), NUM_THREADS, SMEM_BYTES, stream>>>(tmA, tmB,
-                                                                                       args);
+        const int items = p.qtiles * p.nslices;
+        scan_mma_kernel<<<std::min(items, num_sms()), NUM_THREADS, SMEM_BYTES, stream>>>(tmA, tmB,
+                                                                                        args);
     }
     if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
     return launch_final_merge(lists, meta, tau, nq, p.nslices, k, ids, dist, stream);

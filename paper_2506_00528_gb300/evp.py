@@ -73,6 +73,17 @@ SIGNATURES = {
     "evp_server_reset_stats": (_i32, [_p]),
     "evp_server_pause": (_i32, [_p, _i32]),
     "evp_server_destroy": (_i32, [_p]),
+    "evp_db_codes": (_p, [_p]),
+    "evp_db_search_path_workspace": (_sz, [_p, _i64, _i32, _i32, _i32]),
+    "evp_db_search_path": (_i32, [_p, _p, _i64, _i32, _i32, _p, _p, _p, _sz, _p, _p, _i32]),
+    "evp_autotune": (_i32, [_p, _i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
+                            ctypes.POINTER(ctypes.c_float), _p]),
+    "evp_autotune_clear": (_i32, []),
+    "evp_batch_plan_create": (_i32, [_p, _i32, _i32, _p, ctypes.POINTER(_p)]),
+    "evp_batch_plan_path": (_i32, [_p, _i32]),
+    "evp_batch_plan_workspace": (_sz, [_p]),
+    "evp_batch_run": (_i32, [_p, _p, _p]),
+    "evp_batch_plan_destroy": (_i32, [_p]),
     "evp_timing_enable": (_i32, [_i32]),
     "evp_timing_reset": (_i32, []),
     "evp_timing_read": (_i32, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -396,6 +407,82 @@ class Server:
     def close(self):
         if getattr(self, "handle", None):
             _check(load().evp_server_destroy(self.handle), "evp_server_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchDesc(ctypes.Structure):
+    _fields_ = [("db", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("Qc", ctypes.c_void_p),
+                ("nq", ctypes.c_int64), ("n_shortlist", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("ids", ctypes.c_void_p), ("scores", ctypes.c_void_p), ("dist", ctypes.c_void_p)]
+
+
+def autotune(db: "Database", nq: int, k: int, measure: bool = False, stream=None):
+    """(path, popc_ms, mma_ms) from evp_autotune (timings only when measured)."""
+    path = ctypes.c_int32(0)
+    pm, mm = ctypes.c_float(0.0), ctypes.c_float(0.0)
+    args = (ctypes.byref(pm), ctypes.byref(mm)) if measure else (None, None)
+    _check(load().evp_autotune(db.handle, int(nq), int(k), ctypes.byref(path), *args,
+                               _stream_handle(stream)), "evp_autotune")
+    return int(path.value), (pm.value if measure else None), (mm.value if measure else None)
+
+
+class BatchPlan:
+    """evp_batch_plan_*: a list of search / kNN batches planned once and run
+    (optionally as one captured CUDA graph).  Each item of `batches` is a dict
+    with db, and either Q (float32 [nq, d]) + n_shortlist + k (search) or Qc
+    (packed codes) + k (kNN); outputs are allocated here."""
+
+    def __init__(self, batches, graph: bool = True, tune: bool = True, stream=None):
+        self.items = []
+        descs = (BatchDesc * len(batches))()
+        for i, b in enumerate(batches):
+            db = b["db"]
+            k = int(b["k"])
+            if b.get("Q") is not None:
+                Q = b["Q"]
+                _req(Q, torch.float32, "Q")
+                nq = Q.shape[0]
+                ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+                sc = torch.empty((nq, k), dtype=torch.float32, device=Q.device)
+                descs[i] = BatchDesc(db.handle, _ptr(Q), None, nq, int(b["n_shortlist"]), k,
+                                     _ptr(ids), _ptr(sc), None)
+                self.items.append((Q, ids, sc))
+            else:
+                Qc = b["Qc"]
+                _req(Qc, torch.int64, "Qc")
+                nq = Qc.shape[0]
+                ids = torch.empty((nq, k), dtype=torch.int64, device=Qc.device)
+                dist = torch.empty((nq, k), dtype=torch.int32, device=Qc.device)
+                descs[i] = BatchDesc(db.handle, None, _ptr(Qc), nq, 0, k, _ptr(ids), None,
+                                     _ptr(dist))
+                self.items.append((Qc, ids, dist))
+        self.dbs = [b["db"] for b in batches]
+        flags = (1 if graph else 0) | (0 if tune else 2)
+        h = ctypes.c_void_p()
+        _check(load().evp_batch_plan_create(descs, len(batches), flags, _stream_handle(stream),
+                                            ctypes.byref(h)), "evp_batch_plan_create")
+        self.handle = h
+        self._descs = descs
+
+    def path(self, i: int) -> int:
+        return int(load().evp_batch_plan_path(self.handle, int(i)))
+
+    def run(self, status=None, stream=None):
+        _check(load().evp_batch_run(self.handle, _ptr(status), _stream_handle(stream)),
+               "evp_batch_run")
+
+    def outputs(self, i: int):
+        return self.items[i][1], self.items[i][2]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(load().evp_batch_plan_destroy(self.handle), "evp_batch_plan_destroy")
             self.handle = None
 
     def __del__(self):

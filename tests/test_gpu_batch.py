@@ -1,0 +1,82 @@
+"""Batched form: uneven batches against three resident databases, planned
+once (autotuned paths), run eagerly and as a captured CUDA graph; every
+batch equals its own evp_db_search / evp_db_knn call."""
+import pytest
+import torch
+
+from paper_2506_00528_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dbs(dev, evp_lib):
+    out = []
+    for i, (n, d, x) in enumerate([(20_000, 384, 128), (30_000, 768, 256), (15_000, 1024, 384)]):
+        U = torch.from_numpy(synth.mixture_numpy(n, d, n_centres=32, anisotropic=True,
+                                                 stream=1000 + i)).to(dev)
+        T = evp_lib.encode(U, x)
+        out.append((evp_lib.Database(T, U, d, x), U, d, x))
+    yield out
+    for db, *_ in out:
+        db.close()
+
+
+def _batches(evp_lib, dbs, dev):
+    sizes = [1, 5, 17, 200, 3, 64, 129, 1, 31, 400, 16, 2]
+    spec = []
+    for i, nq in enumerate(sizes):
+        db, U, d, x = dbs[i % 3]
+        Q = torch.from_numpy(synth.mixture_numpy(nq, d, n_centres=32, anisotropic=True,
+                                                 stream=2000 + i)).to(dev)
+        if i % 4 == 3:    # plain kNN on packed codes
+            spec.append({"db": db, "Qc": evp_lib.encode(Q, x), "k": 100 if i % 8 == 3 else 10})
+        else:             # whole path: shortlist 10k, rerank to k
+            k = 10 if i % 2 else 5
+            spec.append({"db": db, "Q": Q, "n_shortlist": 10 * k, "k": k})
+    return spec
+
+
+def _alone(evp_lib, b):
+    if "Q" in b:
+        return b["db"].search(b["Q"], b["n_shortlist"], b["k"])
+    return b["db"].knn(b["Qc"], b["k"])
+
+
+@pytest.mark.parametrize("graph,tune", [(True, True), (False, False)])
+def test_batch_plan_matches_per_batch_calls(evp_lib, dev, dbs, graph, tune):
+    spec = _batches(evp_lib, dbs, dev)
+    stream = torch.cuda.Stream()
+    plan = evp_lib.BatchPlan(spec, graph=graph, tune=tune, stream=stream)
+    for i in range(len(spec)):
+        assert plan.path(i) in ((1, 2) if tune else (0,))
+    st = evp_lib.new_status(dev)
+    with torch.cuda.stream(stream):
+        plan.run(status=st, stream=stream)     # capture (graph) or eager
+    stream.synchronize()
+    first = [tuple(t.clone() for t in plan.outputs(i)) for i in range(len(spec))]
+    for o in plan.outputs(0):
+        o.fill_(-9)
+    with torch.cuda.stream(stream):
+        plan.run(status=st, stream=stream)     # replay
+    stream.synchronize()
+    assert int(st.item()) == 0
+    for i, b in enumerate(spec):
+        ref = _alone(evp_lib, b)
+        torch.cuda.synchronize()
+        got = plan.outputs(i)
+        for r, g, f in zip(ref, got, first[i]):
+            assert torch.equal(r, g), i
+            assert torch.equal(r, f), i
+    plan.close()
+
+
+def test_autotune_caches_and_reports(evp_lib, dbs):
+    db = dbs[1][0]
+    evp_lib.load().evp_autotune_clear()
+    path, pm, mm = evp_lib.autotune(db, 256, 10, measure=True)
+    assert path in (1, 2) and pm > 0 and mm > 0
+    assert path == (2 if mm < pm else 1)
+    assert evp_lib.autotune(db, 200, 10)[0] == path     # same bucket -> cached
+    path_big_k, pm2, mm2 = evp_lib.autotune(db, 4, 500, measure=True)
+    assert path_big_k == 1                               # k above the tensor-core limit
