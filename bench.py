@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--path", type=int, default=0, help="0 auto, 1 popcount, 2 tensor core")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the batched-form and served-form measurements")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
+    ap.add_argument("--serve-rate", type=float, default=40.0, help="requests/s (Poisson)")
     return ap.parse_args()
 
 
@@ -149,6 +153,119 @@ def cpu_oracle_sample(U_dev, Q_host, x, shortlist, k, n_total, n_rows=200_000, n
         "seconds": t3 - t0}
 
 
+def measure_batched(evp, synth, dev, seed_batches=64):
+    """Batched form: three resident databases (1M x 384 at x = 128, 4M x 768
+    at x = 256, 2M x 1024 at x = 384), 64 kNN batches with sizes
+    round(logU[1, 8192]) and k in {10, 100}, each against a database drawn
+    at random; one captured graph (autotuned paths) vs one plain launch per
+    batch (automatic path) on the same inputs."""
+    import torch
+    rng = np.random.default_rng(20250601)
+    shapes = [(1_000_000, 384, 128), (4_000_000, 768, 256), (2_000_000, 1024, 384)]
+    dbs = []
+    for i, (n, d, x) in enumerate(shapes):
+        U = synth.mixture_torch(n, d, n_centres=1024, anisotropic=True, stream=40 + i, device=dev)
+        T = evp.encode(U, x)
+        del U
+        dbs.append((evp.Database(T, None, d, x), T, d, x))
+    sizes = np.clip(np.rint(np.exp(rng.uniform(0, np.log(8192), seed_batches))), 1, 8192).astype(int)
+    ks = rng.choice([10, 100], seed_batches)
+    which = rng.integers(0, 3, seed_batches)
+    spec = []
+    for i in range(seed_batches):
+        db, T, d, x = dbs[which[i]]
+        Q = synth.mixture_torch(int(sizes[i]), d, n_centres=1024, anisotropic=True,
+                                stream=100 + i, device=dev)
+        spec.append({"db": db, "Qc": evp.encode(Q, x), "k": int(ks[i])})
+    stream = torch.cuda.Stream(dev)
+    plan = evp.BatchPlan(spec, graph=True, tune=True, stream=stream)
+    with torch.cuda.stream(stream):
+        plan.run(stream=stream)          # capture + first run
+        plan.run(stream=stream)
+    stream.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(reps):
+            plan.run(stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    graph_ms = e0.elapsed_time(e1) / reps
+    outs = [tuple(t.clone() for t in plan.outputs(i)) for i in range(len(spec))]
+    # plain: one evp_db_knn launch per batch, automatic path
+    ws = {}
+    plain_out = [None] * len(spec)
+
+    def plain():
+        for i, b in enumerate(spec):
+            plain_out[i] = b["db"].knn(b["Qc"], b["k"], stream=stream)
+
+    with torch.cuda.stream(stream):
+        plain()
+        e0.record(stream)
+        for _ in range(reps):
+            plain()
+        e1.record(stream)
+    stream.synchronize()
+    plain_ms = e0.elapsed_time(e1) / reps
+    same = all(torch.equal(o[0], p[0]) and torch.equal(o[1], p[1]) for o, p in zip(outs, plain_out))
+    total_q = int(sizes.sum())
+    paths = [plan.path(i) for i in range(len(spec))]
+    plan.close()
+    for db, *_ in dbs:
+        db.close()
+    del ws
+    return {"batches": seed_batches, "queries": total_q,
+            "graph_qps": total_q / (graph_ms / 1e3), "graph_ms": graph_ms,
+            "plain_qps": total_q / (plain_ms / 1e3), "plain_ms": plain_ms,
+            "paths": {"popc": paths.count(1), "mma": paths.count(2)},
+            "identical_results": bool(same),
+            "workload": "3 DBs (1Mx384 x128, 4Mx768 x256, 2Mx1024 x384), 64 kNN batches "
+                        "logU[1,8192] queries, k in {10,100}"}
+
+
+def measure_served(evp, synth, db, d, seconds, rate, dev):
+    """Served form: Poisson arrivals at `rate` requests/s for `seconds`,
+    request sizes round(logU[1, 1024]) queries, k in {10, 100}, shortlist
+    10 k (capped at 1024) reranked to k, continuous batching over 3 slots."""
+    import torch
+    rng = np.random.default_rng(20250602)
+    n_req = max(1, int(seconds * rate))
+    arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    sizes = np.clip(np.rint(np.exp(rng.uniform(0, np.log(1024), n_req))), 1, 1024).astype(int)
+    ks = rng.choice([10, 100], n_req)
+    pool = synth.mixture_torch(4096, d, n_centres=1024, anisotropic=True, stream=77,
+                               device=dev).cpu().pin_memory()
+    srv = evp.Server(db, max_batch_queries=4096, max_k=100, shortlist_factor=10, max_slots=3,
+                     mem_budget_bytes=48 << 30)
+    # warm-up request of each class
+    for k in (10, 100):
+        srv.wait(srv.submit(pool[:64], k))
+    srv.reset_stats()
+    t0 = time.perf_counter()
+    rids = []
+    for i in range(n_req):
+        now = time.perf_counter() - t0
+        if arr[i] > now:
+            time.sleep(arr[i] - now)
+        off = int(rng.integers(0, 4096 - sizes[i] + 1))
+        rids.append(srv.submit(pool[off:off + sizes[i]], int(ks[i])))
+    for r in rids:
+        srv.wait(r, timeout_s=600)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    slots = srv.slots
+    srv.close()
+    return {"requests": n_req, "queries": int(sizes.sum()), "rate_req_s": rate,
+            "qps": int(sizes.sum()) / wall, "p50_ms": st["p50_us"] / 1e3,
+            "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+            "batches": st["batches"], "slots": slots, "wall_s": wall,
+            "workload": "10Mx768 resident, Poisson arrivals, sizes logU[1,1024], "
+                        "k in {10,100}, shortlist 10k reranked"}
+
+
 def main_reference(a):
     """CPU oracle on the same workload, one bounded sample per step."""
     import torch
@@ -195,6 +312,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2506_00528_gb300 import build as _build
+    from paper_2506_00528_gb300 import dist as evp_dist
     from paper_2506_00528_gb300 import evp, synth
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -282,12 +400,11 @@ def main():
                   ("encode", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
                                "final_merge", "rerank")}
     evp.check_status(st, "timed steps")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    # replicas: every rank searched its own B queries per step; the job's
+    # throughput is all ranks' queries over the slowest rank's time
+    total_q, ms = evp_dist.aggregate(B * a.steps, ms, device=dev)
     ms_per_step = ms / a.steps
-    value = world * B * a.steps / (ms / 1000.0)
+    value = total_q / (ms / 1000.0)
 
     # ---- end to end through the API with host buffers (pinned)
     Qh = [q.cpu().pin_memory() for q in Qb]
@@ -316,11 +433,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * B * a.steps / (e2e_ms / 1000.0)
+    e2e_q, e2e_ms = evp_dist.aggregate(B * a.steps, e2e_ms, device=dev)
+    e2e_value = e2e_q / (e2e_ms / 1000.0)
 
     # ---- roofline of the dominant kernel
     hbm_peak, bf16_peak, peak_src = load_peaks()
@@ -395,6 +509,13 @@ def main():
                                                for a_, b_ in zip(got_tern, truth)])),
             "queries": nrq}
 
+    # ---- batched and served forms (rank 0, N = 1)
+    forms = None
+    if not a.no_forms and world == 1:
+        served = measure_served(evp, synth, db, d, a.serve_seconds, a.serve_rate, dev)
+        batched = measure_batched(evp, synth, dev)
+        forms = {"batched": batched, "served": served}
+
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1)
     cpu = None
     if not a.no_cpu_baseline and world == 1:
@@ -420,6 +541,7 @@ def main():
             "roofline": roofline,
             "kernels": kernels,
             "recall_at_10": recall,
+            "forms": forms,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "queries/s",
                     "h2d_bytes_per_step": B * d * 4, "d2h_bytes_per_step": B * k * 12},

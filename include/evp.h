@@ -190,6 +190,26 @@ int32_t ternary_knn_path(const uint64_t* Q, int64_t nq, const uint64_t* S, int64
                          int32_t path);
 
 /* ---------------------------------------------------------------------
+ * evp_merge_topk -- merge per-shard kNN results into the global top-k.
+ *
+ * For a database split into row shards (e.g. one per GPU, Sec. 5.3's
+ * exhaustive search run on each part), ids [nlists][nq][k] (int64,
+ * global row ids in [0, 2^31)) and dist [nlists][nq][k] (int32 Delta), each
+ * list sorted by (Delta, id) as ternary_knn returns them, are merged per
+ * query into the k smallest (Delta, id) pairs.  A list may end early with
+ * id -1 (a shard with fewer than k rows).  The result equals ternary_knn
+ * over the whole database when every shard returned its own k nearest.
+ * Workspace: evp_merge_topk_workspace(...) bytes, 256-byte aligned.
+ * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_UNSUPPORTED (k > EVP_MAX_K or
+ * nlists > 1024), EVP_ERR_NO_MEMORY or EVP_ERR_CUDA; dev_status receives
+ * EVP_ERR_RANGE for an id >= 2^31.
+ * ------------------------------------------------------------------- */
+size_t evp_merge_topk_workspace(int64_t nq, int32_t nlists, int32_t k);
+int32_t evp_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int32_t nlists,
+                       int32_t k, int64_t* out_ids, int32_t* out_dist, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
  * rerank -- re-order a shortlist by the original vectors (Sec. 5.3: n > k
  * proxy results are re-ordered in the original space and the best k
  * kept).
@@ -400,7 +420,7 @@ int32_t evp_server_destroy(evp_server_t s);
  * on its stream around each launch of the library's kernels; (0) stops
  * recording.  evp_timing_read synchronises on the recorded events and
  * returns, for the kernel family `name` ("encode", "scan_init",
- * "scan_popc", "unpack_fp8", "scan_mma", "final_merge", "rerank"), the number of launches and their total
+ * "scan_popc", "unpack_fp8", "scan_mma", "final_merge", "pack_lists", "rerank"), the number of launches and their total
  * duration in milliseconds since the last evp_timing_reset.  Returns
  * EVP_OK, EVP_ERR_INVALID (null outputs) or EVP_ERR_CUDA.  Enabling adds
  * two event records per launch; leave it off outside measurements.

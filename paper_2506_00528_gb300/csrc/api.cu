@@ -177,6 +177,23 @@ int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns
                             EVP_PATH_AUTO);
 }
 
+size_t evp_merge_topk_workspace(int64_t nq, int32_t nlists, int32_t k) {
+    if (nq <= 0 || nlists < 1 || k < 1) return 0;
+    return merge_topk_workspace(nq, nlists, k);
+}
+
+int32_t evp_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int32_t nlists,
+                       int32_t k, int64_t* out_ids, int32_t* out_dist, void* ws, size_t ws_bytes,
+                       int32_t* dev_status, void* stream) {
+    if (nq < 0 || nlists < 1 || k < 1) return EVP_ERR_INVALID;
+    if (k > EVP_MAX_K || nlists > 1024) return EVP_ERR_UNSUPPORTED;
+    if (nq == 0) return EVP_OK;
+    if (!ids || !dist || !out_ids || !out_dist || !ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+        return EVP_ERR_INVALID;
+    return run_merge_topk(ids, dist, nq, nlists, k, out_ids, out_dist, ws, ws_bytes, dev_status,
+                          static_cast<cudaStream_t>(stream));
+}
+
 int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d,
                const int64_t* shortlist, int32_t n, int32_t k, int64_t* ids, float* scores,
                int32_t* dev_status, void* stream) {

@@ -180,6 +180,11 @@ int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uin
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
                            cudaStream_t stream);
 
+size_t merge_topk_workspace(int64_t nq, int nlists, int k);
+int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int nlists, int k,
+                       int64_t* out_ids, int32_t* out_dist, void* ws, size_t ws_bytes,
+                       int32_t* status, cudaStream_t stream);
+
 struct MmaPlan {
     int kp;                 // K padded to a multiple of 128
     int qtiles;             // 128-query tiles

@@ -124,6 +124,37 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// Issue a 32-column TMEM load without waiting for it.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+}
+
+// Wait for the warp's outstanding TMEM loads; v is an in-out operand so that
+// no use of the loaded registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+          "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]),
+          "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]),
+          "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+          "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]),
+          "+r"(v[31])
+        :
+        : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -368,18 +399,18 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // keys all slices of this query have inserted.  Those are real rows,
         // so no row with Delta/2 > T can be among the k nearest.
         auto refresh_union = [&]() {
-            const uint32_t lo = *reinterpret_cast<volatile uint32_t*>(&a.minhalf[qrow]);
+            const uint32_t lo = __ldcg(&a.minhalf[qrow]);
             if (lo == 0xFFFFFFFFu) return;
             const uint32_t hi = min(uthr, (uint32_t)(a.hist_bins - 1));
             uint32_t cum = 0;
-            for (uint32_t h0 = lo; h0 <= hi; h0 += 8) {
-                uint32_t c8[8];
+            for (uint32_t h0 = lo; h0 <= hi; h0 += 16) {
+                uint32_t c16[16];
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    c8[u] = (h0 + u <= hi) ? *reinterpret_cast<volatile uint32_t*>(&hist[h0 + u]) : 0u;
+                for (int u = 0; u < 16; ++u)
+                    c16[u] = (h0 + u <= hi) ? __ldcg(&hist[h0 + u]) : 0u;
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    cum += c8[u];
+                for (int u = 0; u < 16; ++u) {
+                    cum += c16[u];
                     if (cum >= (uint32_t)k && h0 + u < uthr) {
                         uthr = h0 + u;
                         dglob = (float)(a.x - (int)uthr) - 0.5f;
@@ -401,18 +432,22 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 break;
             }
             tc_fence_after();
-            if (valid_q && (t & 3) == 1) refresh_union();
+            // the union bound moves fast while the slices warm up, slowly after
+            if (valid_q && (t < 16 ? (t & (t - 1)) == 0 && t > 0 : (t & 15) == 0)) refresh_union();
             const int64_t tile_row = row0 + (int64_t)t * MMA_N;
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * MMA_N);
-            for (int c = 0; c < MMA_N / 32; ++c) {
-                uint32_t v[32];
-                __syncwarp();
-                tmem_ld32(tbase + (uint32_t)(c * 32), v);
+            // One 32-column group already in registers: stage the lanes'
+            // candidates (flushing first if a lane's staging could overflow).
+            auto group = [&](const uint32_t (&v)[32], int c) {
                 float mx = __uint_as_float(v[0]);
 #pragma unroll
                 for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(v[j]));
-                const float thr = fmaxf(dtau, dglob);
-                if (!__any_sync(0xffffffffu, valid_q && mx > thr)) continue;
+                float thr = fmaxf(dtau, dglob);
+                if (!__any_sync(0xffffffffu, valid_q && mx > thr)) return;
+                if (__any_sync(0xffffffffu, sc > STAGE_SLOTS - 32)) {
+                    flush();
+                    thr = fmaxf(dtau, dglob);
+                }
                 uint32_t cm = 0;
 #pragma unroll
                 for (int j = 0; j < 32; ++j) cm |= (__uint_as_float(v[j]) > thr ? 1u : 0u) << j;
@@ -421,19 +456,32 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 else if (left < 32) cm &= (1u << left) - 1u;
                 const uint32_t gbase = (uint32_t)(tile_row + c * 32 - row0);
 #pragma unroll
-                for (int jc = 0; jc < 2; ++jc) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        if ((cm >> (jc * 16 + j)) & 1u) {
-                            const uint32_t half_delta =
-                                (uint32_t)(a.x - __float2int_rn(__uint_as_float(v[jc * 16 + j])));
-                            staging[sc * MMA_M + m] =
-                                (half_delta << LOCAL_BITS) | (gbase + (uint32_t)(jc * 16 + j));
-                            ++sc;
-                        }
+                for (int j = 0; j < 32; ++j) {
+                    if ((cm >> j) & 1u) {
+                        const uint32_t half_delta =
+                            (uint32_t)(a.x - __float2int_rn(__uint_as_float(v[j])));
+                        staging[sc * MMA_M + m] = (half_delta << LOCAL_BITS) | (gbase + (uint32_t)j);
+                        ++sc;
                     }
-                    if (__any_sync(0xffffffffu, sc > STAGE_SLOTS - 16)) flush();
                 }
+            };
+            // Two register buffers: the load of the next group is in flight
+            // while the current one is examined.
+            uint32_t va[32], vb[32];
+            __syncwarp();
+            tmem_ld32_async(tbase, va);
+            tmem_wait_ld(va);
+#pragma unroll 1
+            for (int c = 0; c < MMA_N / 32; c += 2) {
+                __syncwarp();
+                tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), vb);
+                group(va, c);
+                __syncwarp();
+                tmem_wait_ld(vb);
+                if (c + 2 < MMA_N / 32) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), va);
+                group(vb, c + 1);
+                __syncwarp();
+                if (c + 2 < MMA_N / 32) tmem_wait_ld(va);
             }
             tc_fence_before();
             mbar_arrive(&acc_empty[b]);

@@ -396,6 +396,35 @@ cudaError_t launch_scan(const CUtensorMap& tmap, const ScanArgs& a, int nslices,
 
 }  // namespace
 
+// Shard results (ids, dist) [nlists][nq][k] -> key lists [nq][nlists][2][k]
+// (buffer 0) and meta (valid length, buffer 0): one warp per (query, list).
+// A list ends at its first id < 0; ids must lie in [0, 2^31).
+__global__ void pack_lists_kernel(const int64_t* __restrict__ ids, const int32_t* __restrict__ dist,
+                                  int64_t nq, int nlists, int k, uint64_t* __restrict__ lists,
+                                  int32_t* __restrict__ meta, int32_t* __restrict__ status) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= nq * nlists) return;
+    const int64_t q = w / nlists;
+    const int s = (int)(w - q * nlists);
+    const int64_t src = ((int64_t)s * nq + q) * k;
+    uint64_t* dst = lists + ((q * nlists + s) * 2) * k;
+    int len = k;
+    for (int i0 = 0; i0 < k; i0 += 32) {
+        const int i = i0 + lane;
+        const int64_t id = i < k ? ids[src + i] : -1;
+        const unsigned bad = __ballot_sync(0xffffffffu, i < k && (id < 0 || id >= (int64_t(1) << 31)));
+        if (bad) len = min(len, i0 + __ffs(bad) - 1);
+        if (i < k && id >= 0 && id < (int64_t(1) << 31))
+            dst[i] = ((uint64_t)(uint32_t)dist[src + i] << 32) | (uint64_t)id;
+        if (i < k && id >= (int64_t(1) << 31)) report(status, EVP_ERR_RANGE);
+    }
+    if (lane == 0) {
+        meta[(q * nlists + s) * 2] = len;
+        meta[(q * nlists + s) * 2 + 1] = 0;
+    }
+}
+
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
                            cudaStream_t stream) {
@@ -414,6 +443,27 @@ int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uin
     final_merge_kernel<<<(unsigned)nq, FM_THREADS, smem, stream>>>(lists, meta, nslices, k,
                                                                    key_bits, stage, ids, dist);
     return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+size_t merge_topk_workspace(int64_t nq, int nlists, int k) {
+    return align_up((size_t)nq * nlists * 2 * k * 8, 256) + align_up((size_t)nq * nlists * 2 * 4, 256);
+}
+
+int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int nlists, int k,
+                       int64_t* out_ids, int32_t* out_dist, void* ws, size_t ws_bytes,
+                       int32_t* status, cudaStream_t stream) {
+    if (ws_bytes < merge_topk_workspace(nq, nlists, k)) return EVP_ERR_NO_MEMORY;
+    uint64_t* lists = static_cast<uint64_t*>(ws);
+    int32_t* meta = reinterpret_cast<int32_t*>(static_cast<uint8_t*>(ws) +
+                                               align_up((size_t)nq * nlists * 2 * k * 8, 256));
+    const int64_t warps = nq * nlists;
+    {
+        TimedLaunch timer("pack_lists", stream);
+        pack_lists_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, stream>>>(
+            ids, dist, nq, nlists, k, lists, meta, status);
+    }
+    if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
+    return launch_final_merge(lists, meta, nullptr, nq, nlists, k, out_ids, out_dist, stream);
 }
 
 ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k) {

@@ -54,6 +54,8 @@ SIGNATURES = {
                                 _i32]),
     "ternary_knn_static": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
     "rerank": (_i32, [_p, _i64, _p, _i64, _i32, _p, _i32, _i32, _p, _p, _p, _p]),
+    "evp_merge_topk_workspace": (_sz, [_i64, _i32, _i32]),
+    "evp_merge_topk": (_i32, [_p, _p, _i64, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
     "evp_db_create": (_i32, [_p, _p, _i64, _i32, _i32, _i32, _p, ctypes.POINTER(_p)]),
     "evp_db_destroy": (_i32, [_p]),
     "evp_db_knn_workspace": (_sz, [_p, _i64, _i32, _i32]),
@@ -214,6 +216,21 @@ def ternary_knn_static(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
                                    _stream_handle(stream))
     _check(rc, "ternary_knn_static")
     return ids, dist
+
+
+def merge_topk(ids: torch.Tensor, dist: torch.Tensor, k: int, status=None, stream=None):
+    """evp_merge_topk: per-shard results ids/dist [nlists, nq, k] -> global top-k [nq, k]."""
+    _req(ids, torch.int64, "ids")
+    _req(dist, torch.int32, "dist")
+    nlists, nq = ids.shape[0], ids.shape[1]
+    out_i = torch.empty((nq, k), dtype=torch.int64, device=ids.device)
+    out_d = torch.empty((nq, k), dtype=torch.int32, device=ids.device)
+    need = int(load().evp_merge_topk_workspace(nq, nlists, int(k)))
+    ws = torch.empty(max(need, 256), dtype=torch.uint8, device=ids.device)
+    _check(load().evp_merge_topk(_ptr(ids), _ptr(dist), nq, nlists, int(k), _ptr(out_i),
+                                 _ptr(out_d), _ptr(ws), ws.numel(), _ptr(status),
+                                 _stream_handle(stream)), "evp_merge_topk")
+    return out_i, out_d
 
 
 def rerank(Q: torch.Tensor, S: torch.Tensor, shortlist: torch.Tensor, k: int,
