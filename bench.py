@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-form and served-form measurements")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
-    ap.add_argument("--serve-rate", type=float, default=40.0, help="requests/s (Poisson)")
+    ap.add_argument("--serve-rate", type=float, default=150.0, help="requests/s (Poisson)")
     return ap.parse_args()
 
 

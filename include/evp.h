@@ -128,6 +128,8 @@ int32_t evp_encode(const float* U, int64_t n, int32_t d, int32_t x,
  *   dist       [nq][k] int32 output: Delta of each returned row.
  *   ws         device workspace of at least ternary_knn_workspace(...)
  *              bytes, 256-byte aligned; its contents on entry are ignored.
+ *              The size returned for nq queries also serves every call
+ *              with fewer queries and the same other arguments.
  *   ws_bytes   size of ws.
  * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_NO_MEMORY (ws_bytes too small),
  * EVP_ERR_UNSUPPORTED (d > EVP_MAX_D_SCAN or k > EVP_MAX_K) or
@@ -170,16 +172,17 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
  *   EVP_PATH_MMA   tensor-core scan (tcgen05, e4m3 operands holding -1/0/+1,
  *                  float32 accumulation, exact): the codes are expanded to
  *                  one byte per element (in the workspace when S is given
- *                  packed); requires k <= 128.
- *   EVP_PATH_AUTO  MMA when nq > 16 and k <= 128, POPC otherwise.  This is
- *                  what ternary_knn uses.
+ *                  packed).  A 128-query tile serves all 128 queries for
+ *                  k <= 128 and fewer (64, 32, 16) for larger k.
+ *   EVP_PATH_AUTO  MMA when nq > 16, POPC otherwise.  This is what
+ *                  ternary_knn uses.
  * The MMA path assumes every code has exactly x non-zeros (as evp_encode
  * produces): it computes Delta as 2x - 2*b2sp.  The POPC path computes
  * ||q - s||^2 directly. */
 #define EVP_PATH_AUTO 0
 #define EVP_PATH_POPC 1
 #define EVP_PATH_MMA  2
-#define EVP_MMA_MAX_K 128
+#define EVP_MMA_MAX_K 1024
 
 size_t ternary_knn_path_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k,
                                   int32_t path);
@@ -268,7 +271,8 @@ int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d
  * memory makes the copies truly asynchronous).
  *
  * Workspaces are caller-owned device memory (256-byte aligned) of at least
- * the size the matching *_workspace call returns.
+ * the size the matching *_workspace call returns; the size for nq queries
+ * also serves every call with fewer queries and the same other arguments.
  * ------------------------------------------------------------------- */
 typedef struct evp_db* evp_db_t;
 #define EVP_DB_TENSOR_COPY 1

@@ -131,6 +131,28 @@ int resolve_path(int64_t nq, int32_t k, int32_t path) {
     return path;
 }
 
+}  // namespace
+
+size_t evp::knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert_db) {
+    if (nq <= 0) return 0;
+    size_t best = 0;
+    // popcount path: its workspace does not depend on nq
+    if (path == EVP_PATH_POPC || (path == EVP_PATH_AUTO && resolve_path(1, k, path) == EVP_PATH_POPC))
+        best = plan_popc_scan(std::min<int64_t>(nq, 16), ns, d, k).ws_bytes;
+    // tensor path, taken by AUTO from nq0 queries up: the slice count depends
+    // on the number of query tiles, so the lists can need more room at fewer
+    // queries; the largest call in each tile count is the last one
+    const int64_t nq0 = path == EVP_PATH_MMA ? 1 : 17;
+    if ((path == EVP_PATH_MMA || path == EVP_PATH_AUTO) && k <= MMA_K_MAX && nq >= nq0) {
+        const int64_t qa = mma_active_queries(k);
+        for (int64_t t = (nq0 + qa - 1) / qa; t <= (nq + qa - 1) / qa; ++t)
+            best = std::max(best, plan_mma_scan(std::min(nq, t * qa), ns, d, k, convert_db).ws_bytes);
+    }
+    return best;
+}
+
+namespace {
+
 int32_t check_knn_args(int64_t nq, int64_t ns, int32_t d, int32_t x, int32_t k, int32_t path) {
     if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
         (int64_t)k > ns || path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
@@ -146,9 +168,7 @@ extern "C" {
 
 size_t ternary_knn_path_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k, int32_t path) {
     if (nq <= 0 || ns <= 0 || d < 1 || k < 1) return 0;
-    if (resolve_path(nq, k, path) == EVP_PATH_MMA)
-        return plan_mma_scan(nq, ns, d, k, /*convert_db=*/true).ws_bytes;
-    return plan_popc_scan(nq, ns, d, k).ws_bytes;
+    return knn_ws_bound(nq, ns, d, k, path, /*convert_db=*/true);
 }
 
 size_t ternary_knn_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k) {

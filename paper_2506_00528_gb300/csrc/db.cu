@@ -26,9 +26,7 @@ int resolve_db_path(int64_t nq, int32_t k, int32_t path) {
 }
 
 size_t db_knn_ws(const evp_db* db, int64_t nq, int32_t k, int32_t path) {
-    if (resolve_db_path(nq, k, path) == EVP_PATH_MMA)
-        return plan_mma_scan(nq, db->ns, db->d, k, db->S8 == nullptr).ws_bytes;
-    return plan_popc_scan(nq, db->ns, db->d, k).ws_bytes;
+    return knn_ws_bound(nq, db->ns, db->d, k, path, db->S8 == nullptr);
 }
 
 struct SearchLayout {

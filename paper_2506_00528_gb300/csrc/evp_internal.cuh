@@ -187,13 +187,18 @@ int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int 
 
 struct MmaPlan {
     int kp;                 // K padded to a multiple of 128
-    int qtiles;             // 128-query tiles
+    int qa;                 // active queries per 128-row tile
+    int qtiles;             // query tiles (of qa queries)
     int nslices;            // database slices per query tile
     int64_t rows_per_slice;
     size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, hist_bytes, ws_bytes;
 };
-constexpr int MMA_K_MAX = 128;  // largest k of the tensor-core path
+constexpr int MMA_K_MAX = 1024;  // largest k of the tensor-core path
 int mma_kp(int d);
+// Workspace bytes that serve every kNN call with at most nq queries (and
+// the same other arguments) on `path` (AUTO resolved per call).
+size_t knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert_db);
+int mma_active_queries(int k);
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db);
 cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
                               cudaStream_t stream);

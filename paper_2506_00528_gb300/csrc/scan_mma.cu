@@ -18,6 +18,8 @@
 //               (M=128, N=256, K=32) from one thread into one of two
 //               accumulators (256 columns each), commits stage releases and
 //               accumulator-ready signals with tcgen05.commit;
+//   warp 6      threshold helper: recomputes each query's union bound (below)
+//               from the workspace histogram and publishes it in shared memory;
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator (thread = TMEM lane
 //               = query), Delta from D, and a private max-heap of the k best
 //               (Delta/2 << 20 | row-in-slice) keys in shared memory.  A row
@@ -50,19 +52,20 @@ constexpr int MMA_N = 256;
 constexpr int MMA_K = 32;
 constexpr int KCHUNK = 128;
 constexpr int STAGES = 3;
-constexpr int HEAP_K_MAX = 128;
-constexpr int NUM_THREADS = 192;
+constexpr int HEAP_SLOTS = 128 * 128;  // heap capacity: active queries x k <= 128 x 128
+constexpr int NUM_THREADS = 224;  // TMA, MMA, 4 epilogue warps, threshold helper
 constexpr int A_STAGE_BYTES = MMA_M * KCHUNK;
 constexpr int B_STAGE_BYTES = MMA_N * KCHUNK;
 constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
-constexpr int HEAP_BYTES = HEAP_K_MAX * MMA_M * 4;
+constexpr int HEAP_BYTES = HEAP_SLOTS * 4;
 constexpr int STAGE_SLOTS = 32;                     // per-thread candidate staging
 constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
 constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
+constexpr int UBOUND_BYTES = MMA_M * 8;             // helper -> epilogue thresholds
 constexpr size_t SMEM_BYTES =
-    1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES + STAGING_BYTES + 256;
+    1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES + STAGING_BYTES + UBOUND_BYTES + 256;
 
 // Instruction descriptor: D = f32, A = B = e4m3, both K-major, N = 256, M = 128.
 constexpr uint32_t IDESC = (1u << 4)                  // D format f32
@@ -77,6 +80,7 @@ struct MmaArgs {
     int k;
     int64_t rows_per_slice;
     int qtiles, nslices;   // work items = qtiles * nslices
+    int qa;                // active queries per 128-row tile (k <= HEAP_SLOTS / qa)
     uint64_t* lists;       // [nq][nslices][2][k], buffer 0 used
     int32_t* meta;         // [nq][nslices][2]
     uint64_t* tau_global;  // [nq] (unused by the tensor path)
@@ -171,37 +175,38 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Max-heap of u32 keys, element i of thread m at h[i * MMA_M + m].
-__device__ __forceinline__ void heap_sift_down(uint32_t* h, int m, int n, int i) {
-    const uint32_t v = h[i * MMA_M + m];
+// Max-heap of u32 keys, element i of thread m at h[i * qa + m] (qa = active
+// queries per tile).
+__device__ __forceinline__ void heap_sift_down(uint32_t* h, int qa, int m, int n, int i) {
+    const uint32_t v = h[i * qa + m];
     while (true) {
         int c = 2 * i + 1;
         if (c >= n) break;
-        uint32_t cv = h[c * MMA_M + m];
+        uint32_t cv = h[c * qa + m];
         if (c + 1 < n) {
-            const uint32_t c2 = h[(c + 1) * MMA_M + m];
+            const uint32_t c2 = h[(c + 1) * qa + m];
             if (c2 > cv) {
                 cv = c2;
                 ++c;
             }
         }
         if (cv <= v) break;
-        h[i * MMA_M + m] = cv;
+        h[i * qa + m] = cv;
         i = c;
     }
-    h[i * MMA_M + m] = v;
+    h[i * qa + m] = v;
 }
 
-__device__ __forceinline__ void heap_push(uint32_t* h, int m, int n, uint32_t key) {
+__device__ __forceinline__ void heap_push(uint32_t* h, int qa, int m, int n, uint32_t key) {
     int i = n;
     while (i > 0) {
         const int p = (i - 1) >> 1;
-        const uint32_t pv = h[p * MMA_M + m];
+        const uint32_t pv = h[p * qa + m];
         if (pv >= key) break;
-        h[i * MMA_M + m] = pv;
+        h[i * qa + m] = pv;
         i = p;
     }
-    h[i * MMA_M + m] = key;
+    h[i * qa + m] = key;
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -213,8 +218,10 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     uint8_t* stages = smem;
     uint32_t* heap = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES);
     uint32_t* staging = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES);
+    uint64_t* ubound = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES +
+                                                   STAGING_BYTES);  // [MMA_M]: item << 32 | T
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES +
-                                                 STAGING_BYTES);
+                                                 STAGING_BYTES + UBOUND_BYTES);
     uint64_t* full = bars;                 // [STAGES]
     uint64_t* empty = bars + STAGES;       // [STAGES]
     uint64_t* acc_full = bars + 2 * STAGES;      // [2]
@@ -222,6 +229,8 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     uint64_t* done = bars + 2 * STAGES + 4;      // [1]
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    int* cur_item = abort_flag + 1;   // item the epilogue is on
+    int* epi_done = abort_flag + 2;   // epilogue finished (helper stops)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nslices = a.nslices;
@@ -255,8 +264,11 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
         mbar_init(done, 1);
         *abort_flag = 0;
+        *cur_item = -1;
+        *epi_done = 0;
         fence_mbar_init();
     }
+    for (int i = threadIdx.x; i < MMA_M; i += NUM_THREADS) ubound[i] = ~0ull;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
@@ -286,7 +298,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         }
                         uint8_t* st = stages + s * STAGE_BYTES;
                         mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, w.qt * MMA_M);
+                        tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, w.qt * a.qa);
                         tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK,
                                     (int32_t)(w.row0 + (int64_t)t * MMA_N));
                     }
@@ -344,7 +356,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             mma_commit(done);
             mbar_wait_bounded(done, 0);
         }
-    } else {
+    } else if (warp < 6) {
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
         const int m = quarter * 32 + lane;  // TMEM lane = query row in the tile
@@ -355,9 +367,11 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const Item w = item_of(item);
         const int slice = w.slice, ntiles = w.ntiles;
         const int64_t row0 = w.row0, row_end = w.row_end;
-        const int64_t qrow = (int64_t)w.qt * MMA_M + m;
-        const bool valid_q = qrow < a.nq;
+        const int qa = a.qa;
+        const int64_t qrow = (int64_t)w.qt * qa + m;
+        const bool valid_q = m < qa && qrow < a.nq;
         uint32_t* hist = a.hist + (valid_q ? qrow : 0) * (int64_t)a.hist_bins;
+        if (warp == 2 && lane == 0) *reinterpret_cast<volatile int*>(cur_item) = item;
         int hs = 0;
         float dtau = -INFINITY;   // own heap root: accept D > dtau (strict: rows arrive in order)
         float dglob = -INFINITY;  // union bound: accept D >= x - uthr
@@ -376,12 +390,12 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const uint32_t key = staging[i * MMA_M + m];
                     bool ins = false;
                     if (hs < k) {
-                        heap_push(heap, m, hs, key);
+                        heap_push(heap, qa, m, hs, key);
                         ++hs;
                         ins = true;
                     } else if (key < heap[m]) {
                         heap[m] = key;
-                        heap_sift_down(heap, m, hs, 0);
+                        heap_sift_down(heap, qa, m, hs, 0);
                         ins = true;
                     }
                     if (ins) {
@@ -394,30 +408,6 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             if (lmin < old_min) atomicMin(&a.minhalf[qrow], lmin);
             sc = 0;
             if (hs == k) dtau = (float)(a.x - (int)(heap[m] >> LOCAL_BITS));
-        };
-        // Union bound: the smallest T with count(Delta/2 <= T) >= k over the
-        // keys all slices of this query have inserted.  Those are real rows,
-        // so no row with Delta/2 > T can be among the k nearest.
-        auto refresh_union = [&]() {
-            const uint32_t lo = __ldcg(&a.minhalf[qrow]);
-            if (lo == 0xFFFFFFFFu) return;
-            const uint32_t hi = min(uthr, (uint32_t)(a.hist_bins - 1));
-            uint32_t cum = 0;
-            for (uint32_t h0 = lo; h0 <= hi; h0 += 16) {
-                uint32_t c16[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u)
-                    c16[u] = (h0 + u <= hi) ? __ldcg(&hist[h0 + u]) : 0u;
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    cum += c16[u];
-                    if (cum >= (uint32_t)k && h0 + u < uthr) {
-                        uthr = h0 + u;
-                        dglob = (float)(a.x - (int)uthr) - 0.5f;
-                        return;
-                    }
-                }
-            }
         };
         for (int t = 0; t < ntiles; ++t, ++tt) {
             const int b = tt & 1;
@@ -432,8 +422,14 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 break;
             }
             tc_fence_after();
-            // the union bound moves fast while the slices warm up, slowly after
-            if (valid_q && (t < 16 ? (t & (t - 1)) == 0 && t > 0 : (t & 15) == 0)) refresh_union();
+            {   // union bound published by the helper warp for this item
+                const uint64_t ub = *reinterpret_cast<volatile uint64_t*>(&ubound[m]);
+                const uint32_t T = (uint32_t)ub;
+                if ((int)(ub >> 32) == item && T < uthr) {
+                    uthr = T;
+                    dglob = (float)(a.x - (int)uthr) - 0.5f;
+                }
+            }
             const int64_t tile_row = row0 + (int64_t)t * MMA_N;
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * MMA_N);
             // One 32-column group already in registers: stage the lanes'
@@ -492,14 +488,14 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // heap -> ascending order in place, then the (query, slice) list
             for (int n = hs - 1; n > 0; --n) {
                 const uint32_t top = heap[m];
-                heap[m] = heap[n * MMA_M + m];
-                heap[n * MMA_M + m] = top;
-                heap_sift_down(heap, m, n, 0);
+                heap[m] = heap[n * qa + m];
+                heap[n * qa + m] = top;
+                heap_sift_down(heap, qa, m, n, 0);
             }
             uint64_t* out = a.lists + ((qrow * nslices + slice) * 2) * k;
             uint64_t last = KEY_NONE;
             for (int j = 0; j < hs; ++j) {
-                const uint32_t key = heap[j * MMA_M + m];
+                const uint32_t key = heap[j * qa + m];
                 last = ((uint64_t)(2u * (key >> LOCAL_BITS)) << 32) |
                        (uint64_t)(row0 + (key & ((1u << LOCAL_BITS) - 1u)));
                 out[j] = last;
@@ -515,6 +511,61 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         if (!ok) {
             report(a.status, EVP_ERR_TIMEOUT);
             *(volatile int*)abort_flag = 1;
+        }
+        __syncwarp();
+        if (warp == 2 && lane == 0) *reinterpret_cast<volatile int*>(epi_done) = 1;
+    } else {
+        // ---------------- threshold helper ----------------
+        // Union bound of each query of the current item: the smallest T with
+        // count(Delta/2 <= T) >= k over the keys all slices of the query have
+        // inserted (counted in the workspace histogram).  Those are real rows,
+        // so no row with Delta/2 > T can be among the k nearest.  Computed
+        // here, off the epilogue's critical path, and published in shared
+        // memory tagged with the item.
+        uint32_t best[MMA_M / 32];
+        int seen = -1;
+        while (!*reinterpret_cast<volatile int*>(epi_done) &&
+               !*reinterpret_cast<volatile int*>(abort_flag)) {
+            const int item = *reinterpret_cast<volatile int*>(cur_item);
+            if (item < 0) {
+                __nanosleep(1000);
+                continue;
+            }
+            if (item != seen) {
+#pragma unroll
+                for (int j = 0; j < MMA_M / 32; ++j) best[j] = 0xFFFFFFFFu;
+                seen = item;
+            }
+            const int qt = item % a.qtiles;
+#pragma unroll 1
+            for (int j = 0; j < MMA_M / 32; ++j) {
+                const int mm = j * 32 + lane;
+                const int64_t qrow = (int64_t)qt * a.qa + mm;
+                if (mm >= a.qa || qrow >= a.nq) continue;
+                const uint32_t lo = __ldcg(&a.minhalf[qrow]);
+                if (lo == 0xFFFFFFFFu) continue;
+                const uint32_t* hist = a.hist + qrow * (int64_t)a.hist_bins;
+                const uint32_t hi = min(best[j], (uint32_t)(a.hist_bins - 1));
+                uint32_t cum = 0;
+                bool found = false;
+                for (uint32_t h0 = lo; h0 <= hi && !found; h0 += 16) {
+                    uint32_t c16[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) c16[u] = (h0 + u <= hi) ? __ldcg(&hist[h0 + u]) : 0u;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        cum += c16[u];
+                        if (!found && cum >= (uint32_t)a.k && h0 + u < best[j]) {
+                            best[j] = h0 + u;
+                            found = true;
+                        }
+                    }
+                }
+                if (found)
+                    *reinterpret_cast<volatile uint64_t*>(&ubound[mm]) =
+                        ((uint64_t)(uint32_t)item << 32) | best[j];
+            }
+            __nanosleep(2000);
         }
     }
 
@@ -574,10 +625,20 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 int mma_kp(int d) { return (d + KCHUNK - 1) / KCHUNK * KCHUNK; }
 
+// Queries served per 128-row tile: all 128 while their heaps fit
+// (k <= 128); for larger k fewer queries share the tile (the other rows of
+// the tile are computed and ignored), so that active queries x k <= 128^2.
+int mma_active_queries(int k) {
+    int qa = MMA_M;
+    while (qa > 16 && qa * k > HEAP_SLOTS) qa >>= 1;
+    return qa;
+}
+
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
     MmaPlan p{};
     p.kp = mma_kp(d);
-    p.qtiles = (int)((nq + MMA_M - 1) / MMA_M);
+    p.qa = mma_active_queries(k);
+    p.qtiles = (int)((nq + p.qa - 1) / p.qa);
     const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
     const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
     // qtiles * slices a multiple of the SM count (whole waves of the
@@ -619,7 +680,7 @@ cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
 int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint64_t* S,
                     int64_t ns, int d, int x, int k, int64_t* ids, int32_t* dist, void* ws,
                     size_t ws_bytes, int32_t* status, cudaStream_t stream) {
-    if (k > HEAP_K_MAX) return EVP_ERR_UNSUPPORTED;
+    if (k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
     const MmaPlan p = plan_mma_scan(nq, ns, d, k, S8 == nullptr);
     if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
     uint8_t* w = static_cast<uint8_t*>(ws);
@@ -671,6 +732,7 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.k = k;
     args.rows_per_slice = p.rows_per_slice;
     args.qtiles = p.qtiles;
+    args.qa = p.qa;
     args.nslices = p.nslices;
     args.lists = lists;
     args.meta = meta;

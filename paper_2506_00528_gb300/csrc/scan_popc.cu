@@ -242,8 +242,11 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
                 }
             }
             __syncthreads();
-        } else if (tid < QB) {
-            tau[tid] = min(tau[tid], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[tid]));
+        } else if ((it & 7) == 7 && tid >= NT - QB) {
+            // fold in other slices' thresholds now and then, from the last
+            // warp (thread 0 issues the copies and must not wait on L2)
+            const int q = NT - 1 - tid;
+            tau[q] = min(tau[q], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
         }
     }
 
@@ -251,7 +254,7 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         // drain the loads still in flight before the CTA exits
         if (tid == 0) {
             const int issued = min(ntl, it + a.stages);
-            for (int j = it + 1; j < issued; ++j)
+            for (int j = it; j < issued; ++j)
                 if (!mbar_wait_bounded(&bars[j % a.stages], (uint32_t)((j / a.stages) & 1))) break;
         }
         return;

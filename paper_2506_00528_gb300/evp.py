@@ -28,7 +28,7 @@ EVP_ERR_UNSUPPORTED = 6
 EVP_ERR_RANGE = 7
 
 PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
-MMA_MAX_K = 128
+MMA_MAX_K = 1024
 
 MAX_D_ENCODE = 2048
 MAX_D_SCAN = 1024

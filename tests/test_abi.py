@@ -97,3 +97,22 @@ def test_argument_errors_detected_on_host(lib):
     # k > n
     assert lib.rerank(fake, i64(1), fake, i64(5), i32(8), fake, i32(3), i32(4), fake, fake,
                       None, None) == 1
+
+
+@pytest.mark.parametrize("d,ns", [(384, 20_000), (768, 10_000_000), (1024, 3_000)])
+def test_workspace_serves_every_smaller_batch(lib, d, ns):
+    """The workspace size returned for nq queries is enough for any call with
+    fewer queries (servers and batch plans size one buffer for the largest
+    batch): it never decreases as nq grows, on every path and for every k."""
+    f = lib.ternary_knn_path_workspace
+    f.restype = ctypes.c_size_t
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    for path in (0, 1, 2):
+        for k in (1, 5, 20, 100, 200, 1000):
+            if k > ns:
+                continue
+            prev = 0
+            for nq in list(range(1, 600)) + [1023, 1024, 1025, 4096]:
+                w = f(nq, ns, d, k, path)
+                assert w >= prev, (path, k, nq)
+                prev = w

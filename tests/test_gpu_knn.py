@@ -13,8 +13,8 @@ PATHS = [1, 2]   # EVP_PATH_POPC, EVP_PATH_MMA
 
 
 def _run(evp, Tq, Ts, d, x, k, dev, path=0):
-    if path == 2 and k > 128:
-        pytest.skip("tensor-core path takes k <= 128")
+    if path == 2 and k > 1024:
+        pytest.skip("tensor-core path takes k <= 1024")
     st = evp.new_status(dev)
     ids, dist = evp.ternary_knn(torch.from_numpy(Tq.view(np.int64)).to(dev),
                                 torch.from_numpy(Ts.view(np.int64)).to(dev), d, x, k, status=st,
@@ -87,7 +87,7 @@ def test_query_counts_span_passes(evp_lib, dev, nq, path):
     np.testing.assert_array_equal(ids, oi)
 
 
-@pytest.mark.parametrize("path,k", [(1, 300), (2, 128), (1, 1024)])
+@pytest.mark.parametrize("path,k", [(1, 300), (2, 128), (1, 1024), (2, 300), (2, 1024)])
 def test_massive_ties(evp_lib, dev, path, k):
     """Only six distinct codes in the database: almost every Delta ties, so
     the (Delta, index) order decides everything, across slices and merges."""
@@ -144,9 +144,9 @@ def test_argument_errors(evp_lib, dev):
         evp_lib.ternary_knn(big[:1], big, 2048, 10, 3)         # d above the scan limit
     with pytest.raises(evp_lib.EvpError):
         evp_lib.ternary_knn(Vs[:1], Vs, 64, 10, 9, path=3)     # unknown path
-    many = torch.zeros((300, 2), dtype=torch.int64, device=dev)
+    many = torch.zeros((2000, 2), dtype=torch.int64, device=dev)
     with pytest.raises(evp_lib.EvpError):
-        evp_lib.ternary_knn(many[:20], many, 64, 10, 129, path=2)   # k above the MMA limit
+        evp_lib.ternary_knn(many[:20], many, 64, 10, 1025, path=2)  # k above the limit
     ws = torch.empty(256, dtype=torch.uint8, device=dev)
     out = torch.empty(16, dtype=torch.int64, device=dev)
     rc = evp_lib.load().ternary_knn(Vs.data_ptr(), 1, Vs.data_ptr(), 10, 64, 10, 3,
