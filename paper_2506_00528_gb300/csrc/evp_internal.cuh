@@ -190,6 +190,8 @@ struct MmaPlan {
     int qa;                 // active queries per 128-row tile
     int qtiles;             // query tiles (of qa queries)
     int nslices;            // database slices per query tile
+    int cg;                 // CTAs per tensor-core instruction: 1, or 2 (a CTA pair)
+    int workers;            // resident CTAs (cg = 1) or CTA pairs (cg = 2)
     int64_t rows_per_slice;
     size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, hist_bytes, ws_bytes;
 };

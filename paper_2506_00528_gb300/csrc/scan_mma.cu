@@ -9,15 +9,17 @@
 // non-zeros each.  Float8 is used instead of int8 because the dense int8
 // tensor rate of this GPU generation is far below its fp8 rate.
 //
-// Kernel (one CTA per SM; CTA = one tile of 128 queries x one slice of the
-// database):
+// Kernel (persistent: one CTA per SM, or one CTA pair per two SMs, looping
+// over work items = (query tile, database slice)):
 //   warp 0      TMA producer: K-chunks of 128 bytes of the query tile (A,
-//               128 x 128 B) and of the database tile (B, 256 x 128 B),
-//               SWIZZLE_128B, through a ring of STAGES mbarrier stages;
+//               128 x 128 B) and of the database tile (B, 256 x 128 B, or its
+//               half for a CTA pair), SWIZZLE_128B, through a ring of
+//               mbarrier stages;
 //   warp 1      allocates 512 TMEM columns, issues tcgen05.mma
-//               (M=128, N=256, K=32) from one thread into one of two
-//               accumulators (256 columns each), commits stage releases and
-//               accumulator-ready signals with tcgen05.commit;
+//               (M = 128 or, for a pair, 256; N = 256; K = 32) from one thread
+//               into one of two accumulators (256 columns each), commits
+//               stage releases and accumulator-ready signals with
+//               tcgen05.commit (multicast to both CTAs of a pair);
 //   warp 6      threshold helper: recomputes each query's union bound (below)
 //               from the workspace histogram and publishes it in shared memory;
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator (thread = TMEM lane
@@ -29,34 +31,36 @@
 //               of the query inserts is counted in a per-query Delta
 //               histogram in the workspace, and the k-th smallest counted
 //               Delta bounds the answer for all slices.
-//               Each 32-column TMEM load is first reduced to its maximum, so
-//               a warp skips the group when no lane has a candidate;
-//               candidates go to a small per-thread staging buffer, and the
-//               warp inserts all lanes' staged keys into their heaps together
-//               when any lane's buffer fills, so heap updates of different
-//               lanes do not serialise.
+//               Each 32-column TMEM load is reduced to eight 4-column maxima
+//               and their maximum (three-input max); a warp skips the group
+//               when no lane has a candidate, and otherwise examines only the
+//               4-column sub-groups in which some lane has one.  Candidates
+//               go to a per-thread staging buffer that the warp inserts into
+//               the heaps together when a lane's buffer could overflow, so
+//               heap updates of different lanes do not serialise.
 // The Delta matrix is never written to memory.  Per (query, slice) sorted
 // lists go to the workspace and the per-query merge of the popcount path
 // combines them.  Every mbarrier wait is bounded (2 s); on expiry the CTA
-// reports EVP_ERR_TIMEOUT, drains what it issued and frees TMEM.
+// reports EVP_ERR_TIMEOUT, raises an abort flag in itself and its pair
+// peer (every other wait then gives up at once), lets the copies and MMAs
+// already issued land, and frees TMEM.
 #include "evp_internal.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 
 namespace evp {
 
 namespace {
 
-constexpr int MMA_M = 128;
-constexpr int MMA_N = 256;
+constexpr int MMA_M = 128;   // query rows per CTA (= TMEM lanes)
+constexpr int MMA_N = 256;   // database rows per accumulator tile
 constexpr int MMA_K = 32;
 constexpr int KCHUNK = 128;
-constexpr int STAGES = 3;
 constexpr int HEAP_SLOTS = 128 * 128;  // heap capacity: active queries x k <= 128 x 128
 constexpr int NUM_THREADS = 224;  // TMA, MMA, 4 epilogue warps, threshold helper
+constexpr int EPI_WARPS = 4;
 constexpr int A_STAGE_BYTES = MMA_M * KCHUNK;
-constexpr int B_STAGE_BYTES = MMA_N * KCHUNK;
-constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
 constexpr int HEAP_BYTES = HEAP_SLOTS * 4;
 constexpr int STAGE_SLOTS = 32;                     // per-thread candidate staging
 constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
@@ -64,13 +68,29 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
 constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
 constexpr int UBOUND_BYTES = MMA_M * 8;             // helper -> epilogue thresholds
-constexpr size_t SMEM_BYTES =
-    1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES + STAGING_BYTES + UBOUND_BYTES + 256;
 
-// Instruction descriptor: D = f32, A = B = e4m3, both K-major, N = 256, M = 128.
-constexpr uint32_t IDESC = (1u << 4)                  // D format f32
-                           | (0u << 7) | (0u << 10)   // A, B format e4m3
-                           | ((uint32_t)(MMA_N >> 3) << 17) | ((uint32_t)(MMA_M >> 4) << 24);
+// CG = CTAs per tensor-core instruction.  CG = 1: M = 128, each CTA stages
+// its query tile and the whole 256-row database tile.  CG = 2: a CTA pair
+// (cluster of two) runs M = 256, N = 256 instructions issued by the even
+// CTA; each CTA stages its own 128 query rows and one half (128 rows) of
+// the database tile, and holds the accumulator rows of its own queries in
+// its TMEM.  The pair moves a third less operand data per flop through
+// L2 and shared memory.
+template <int CG>
+struct MmaCfg {
+    static constexpr int B_ROWS = MMA_N / CG;  // database rows staged per CTA
+    static constexpr int B_STAGE_BYTES = B_ROWS * KCHUNK;
+    static constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
+    static constexpr int STAGES = CG == 2 ? 4 : 3;
+    static constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES +
+                                         STAGING_BYTES + UBOUND_BYTES + 256;
+    // Instruction descriptor: D = f32, A = B = e4m3 (format 0), both
+    // K-major, N = 256, M = 128 x CG.
+    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(MMA_N >> 3) << 17) |
+                                      ((uint32_t)((MMA_M * CG) >> 4) << 24);
+};
+static_assert(MmaCfg<1>::SMEM_BYTES <= 232448 && MmaCfg<2>::SMEM_BYTES <= 232448,
+              "shared memory per CTA");
 
 struct MmaArgs {
     int nq;
@@ -100,6 +120,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            | (2ull << 61);                      // SWIZZLE_128B
 }
 
+// Maximum of three floats in one instruction (no NaN among the inputs here).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -107,25 +134,115 @@ __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
+template <int CG>
 __device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                        uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-        : "memory");
+    if constexpr (CG == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(MmaCfg<1>::IDESC), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(MmaCfg<2>::IDESC), "r"(accumulate)
+            : "memory");
+    }
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
+// One arrival on `bar` once every MMA issued so far has completed: on this
+// CTA's barrier (CG = 1) or on the barrier at the same offset in both CTAs
+// of the pair (CG = 2).
+template <int CG>
+__device__ __forceinline__ void mma_commit_all(uint64_t* bar) {
+    if constexpr (CG == 1) {
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(bar))
+            : "memory");
+    } else {
+        const uint16_t both = 3;
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster"
+            ".b64 [%0], %1;" ::"r"(smem_u32(bar)),
+            "h"(both)
+            : "memory");
+    }
+}
+
+// The same, arriving on this CTA's barrier only.
+template <int CG>
+__device__ __forceinline__ void mma_commit_self(uint64_t* bar) {
+    if constexpr (CG == 1) {
+        mma_commit_all<1>(bar);
+    } else {
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(bar))
+            : "memory");
+    }
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// ---- CTA-pair helpers (cluster of two) ----------------------------------
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// shared::cluster address of the same shared-memory location in CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
+                 : "memory");
+}
+
+__device__ __forceinline__ void st_cluster_u32(uint32_t addr_cluster, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr_cluster), "r"(v) : "memory");
+}
+
+// Every thread of both CTAs: all shared-memory and barrier operations issued
+// before are visible to the other CTA after.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 2-D tiled load into this CTA's shared memory, its bytes counted on the
+// barrier at shared::cluster address `bar_cluster`, which may be in the
+// other CTA of the pair.
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int32_t c0, int32_t c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(c0), "r"(c1)
+        : "memory");
+}
+
+// Bounded mbarrier wait that also gives up as soon as *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   const int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*reinterpret_cast<const volatile int*>(abort)) return false;
+        if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return true;
 }
 
 // Issue a 32-column TMEM load without waiting for it.
@@ -209,9 +326,13 @@ __device__ __forceinline__ void heap_push(uint32_t* h, int qa, int m, int n, uin
     h[i * qa + m] = key;
 }
 
+template <int CG>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const MmaArgs a) {
+    using C = MmaCfg<CG>;
+    constexpr int STAGES = C::STAGES;
+    constexpr int STAGE_BYTES = C::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -234,19 +355,24 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nslices = a.nslices;
-    const int nitems = a.qtiles * a.nslices;
+    // CTA pair: rank 0 issues the MMAs; both run every other role.
+    const uint32_t rank = CG == 2 ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const int worker = (int)blockIdx.x / CG, nworkers = (int)gridDim.x / CG;
+    const int units = (a.qtiles + CG - 1) / CG;  // query tiles (CG = 1) or tile pairs per slice
+    const int nitems = units * a.nslices;
     const int kchunks = a.kchunks;
-    // Work item -> (query tile, database slice).  Consecutive items share a
-    // slice, so the CTAs of one wave that work on the same slice read its
-    // rows from L2 rather than HBM.
+    // Work item -> (query unit, database slice); this CTA takes query tile
+    // unit * CG + rank.  Consecutive items share a slice, so the CTAs of one
+    // wave that work on the same slice read its rows from L2 rather than HBM.
     struct Item {
         int qt, slice, ntiles;
         int64_t row0, row_end;
     };
     auto item_of = [&](int item) {
         Item w;
-        w.qt = item % a.qtiles;
-        w.slice = item / a.qtiles;
+        w.qt = (item % units) * CG + (int)rank;
+        w.slice = item / units;
         w.row0 = (int64_t)w.slice * a.rows_per_slice;
         w.row_end = min(w.row0 + a.rows_per_slice, a.ns);
         w.ntiles = w.row_end > w.row0 ? (int)((w.row_end - w.row0 + MMA_N - 1) / MMA_N) : 0;
@@ -260,7 +386,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&acc_full[b], 1);
-            mbar_init(&acc_empty[b], MMA_M);
+            mbar_init(&acc_empty[b], CG * EPI_WARPS);  // one arrival per epilogue warp
         }
         mbar_init(done, 1);
         *abort_flag = 0;
@@ -270,59 +396,91 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     }
     for (int i = threadIdx.x; i < MMA_M; i += NUM_THREADS) ubound[i] = ~0ull;
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        // CG = 2: one warp of each CTA of the pair allocates, collectively
+        if constexpr (CG == 1) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "r"(TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if constexpr (CG == 2) cluster_sync_all();  // the peer's barriers are initialised
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // Raise the abort flag here and, for a pair, in the other CTA.
+    auto raise_abort = [&]() {
+        *(volatile int*)abort_flag = 1;
+        if constexpr (CG == 2) st_cluster_u32(peer_addr(abort_flag, rank ^ 1u), 1u);
+    };
 
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
+            // CG = 2: both CTAs' copies are counted on the leader's full
+            // barrier, which expects the bytes of the pair.
             int it = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int item = worker; item < nitems && ok; item += nworkers) {
                 const Item w = item_of(item);
+                // a tile past the last query (odd tile count) loads tile 0; its rows are ignored
+                const int32_t arow = w.qt < a.qtiles ? w.qt * a.qa : 0;
                 for (int t = 0; t < w.ntiles && ok; ++t) {
+                    const int32_t brow = (int32_t)(w.row0 + (int64_t)t * MMA_N + rank * C::B_ROWS);
                     for (int kc = 0; kc < kchunks; ++kc, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                        if (!mbar_wait_bounded(&empty[s], ph ^ 1u) || *(volatile int*)abort_flag) {
+                        if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, abort_flag)) {
                             ok = false;
                             break;
                         }
                         uint8_t* st = stages + s * STAGE_BYTES;
-                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                        tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, w.qt * a.qa);
-                        tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK,
-                                    (int32_t)(w.row0 + (int64_t)t * MMA_N));
+                        if constexpr (CG == 1) {
+                            mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                            tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, arow);
+                            tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK, brow);
+                        } else {
+                            if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
+                            const uint32_t fb = peer_addr(&full[s], 0u);
+                            tma_load_2d_pair(st, &tmA, fb, kc * KCHUNK, arow);
+                            tma_load_2d_pair(st + A_STAGE_BYTES, &tmB, fb, kc * KCHUNK, brow);
+                        }
                     }
                 }
             }
+            if (ok) {
+                // the MMAs have read every stage filled (and, for a pair, the
+                // leader's releases of them have all arrived here)
+                for (int j = max(0, it - STAGES); j < it && ok; ++j)
+                    ok = mbar_wait_or_abort(&empty[j % STAGES], (uint32_t)((j / STAGES) & 1),
+                                            abort_flag);
+            }
             if (!ok) {
-                report(a.status, EVP_ERR_TIMEOUT);
-                *(volatile int*)abort_flag = 1;
-                // let every stage this thread filled land before the CTA exits
-                for (int j = max(0, it - STAGES); j < it; ++j)
-                    mbar_wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1));
+                if (!*(volatile int*)abort_flag) report(a.status, EVP_ERR_TIMEOUT);
+                raise_abort();
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             // ---------------- MMA issuer ----------------
+            // CG = 2: the shared-memory descriptors name this CTA's stage;
+            // the instruction reads the same offsets in the peer CTA.
             int it = 0, tt = 0;
             bool ok = true;
-            for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int item = worker; item < nitems && ok; item += nworkers) {
               const Item w = item_of(item);
               for (int t = 0; t < w.ntiles && ok; ++t, ++tt) {
                 const int b = tt & 1;
                 const uint32_t use = (uint32_t)(tt >> 1);
-                if (!mbar_wait_bounded(&acc_empty[b], (use & 1u) ^ 1u)) {
+                if (!mbar_wait_or_abort(&acc_empty[b], (use & 1u) ^ 1u, abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -331,7 +489,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 for (int kc = 0; kc < kchunks; ++kc, ++it) {
                     const int s = it % STAGES;
                     const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                    if (!mbar_wait_bounded(&full[s], ph) || *(volatile int*)abort_flag) {
+                    if (!mbar_wait_or_abort(&full[s], ph, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -340,20 +498,20 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const uint32_t sb = sa + A_STAGE_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < KCHUNK / MMA_K; ++kk) {
-                        mma_f8(dt, sw128_desc(sa + kk * MMA_K), sw128_desc(sb + kk * MMA_K),
-                               (kc > 0 || kk > 0) ? 1u : 0u);
+                        mma_f8<CG>(dt, sw128_desc(sa + kk * MMA_K), sw128_desc(sb + kk * MMA_K),
+                                   (kc > 0 || kk > 0) ? 1u : 0u);
                     }
-                    mma_commit(&empty[s]);
+                    mma_commit_all<CG>(&empty[s]);
                 }
-                if (ok) mma_commit(&acc_full[b]);
+                if (ok) mma_commit_all<CG>(&acc_full[b]);
               }
             }
             if (!ok) {
-                report(a.status, EVP_ERR_TIMEOUT);
-                *(volatile int*)abort_flag = 1;
+                if (!*(volatile int*)abort_flag) report(a.status, EVP_ERR_TIMEOUT);
+                raise_abort();
             }
             // all issued MMAs complete before TMEM is released
-            mma_commit(done);
+            mma_commit_self<CG>(done);
             mbar_wait_bounded(done, 0);
         }
     } else if (warp < 6) {
@@ -363,7 +521,10 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int k = a.k;
         int tt = 0;  // accumulator tiles consumed so far (all items)
         bool ok = true;
-        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+        // accumulator release: the leader's barrier (in the other CTA for rank 1)
+        const uint32_t acc_empty0 = CG == 2 ? peer_addr(&acc_empty[0], 0u) : 0u;
+        const uint32_t acc_empty1 = CG == 2 ? peer_addr(&acc_empty[1], 0u) : 0u;
+        for (int item = worker; item < nitems && ok; item += nworkers) {
         const Item w = item_of(item);
         const int slice = w.slice, ntiles = w.ntiles;
         const int64_t row0 = w.row0, row_end = w.row_end;
@@ -414,8 +575,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const uint32_t use = (uint32_t)(tt >> 1);
             // one lane waits, the warp follows it (keeps the warp converged)
             int got = 1;
-            if (lane == 0)
-                got = mbar_wait_bounded(&acc_full[b], use & 1u) && !*(volatile int*)abort_flag;
+            if (lane == 0) got = mbar_wait_or_abort(&acc_full[b], use & 1u, abort_flag);
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) {
                 ok = false;
@@ -435,29 +595,41 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // One 32-column group already in registers: stage the lanes'
             // candidates (flushing first if a lane's staging could overflow).
             auto group = [&](const uint32_t (&v)[32], int c) {
-                float mx = __uint_as_float(v[0]);
+                // maxima of the 8 sub-groups of 4 columns, then of the group
+                float sm[8];
 #pragma unroll
-                for (int j = 1; j < 32; ++j) mx = fmaxf(mx, __uint_as_float(v[j]));
+                for (int i = 0; i < 8; ++i)
+                    sm[i] = fmaxf(fmax3(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]),
+                                        __uint_as_float(v[4 * i + 2])),
+                                  __uint_as_float(v[4 * i + 3]));
+                const float mx = fmax3(fmax3(sm[0], sm[1], sm[2]), fmax3(sm[3], sm[4], sm[5]),
+                                       fmaxf(sm[6], sm[7]));
                 float thr = fmaxf(dtau, dglob);
                 if (!__any_sync(0xffffffffu, valid_q && mx > thr)) return;
-                if (__any_sync(0xffffffffu, sc > STAGE_SLOTS - 32)) {
+                // columns of this group inside the slice (the last tile is ragged)
+                const int64_t left = row_end - (tile_row + c * 32);
+                const int lim = !valid_q ? 0 : (left >= 32 ? 32 : (left > 0 ? (int)left : 0));
+                int nsub = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) nsub += (sm[i] > thr && 4 * i < lim) ? 1 : 0;
+                // flush first if this group could overflow a lane's staging
+                if (__any_sync(0xffffffffu, sc + 4 * nsub > STAGE_SLOTS)) {
                     flush();
                     thr = fmaxf(dtau, dglob);
                 }
-                uint32_t cm = 0;
-#pragma unroll
-                for (int j = 0; j < 32; ++j) cm |= (__uint_as_float(v[j]) > thr ? 1u : 0u) << j;
-                const int64_t left = row_end - (tile_row + c * 32);  // rows of this group in range
-                if (!valid_q || left <= 0) cm = 0;
-                else if (left < 32) cm &= (1u << left) - 1u;
                 const uint32_t gbase = (uint32_t)(tile_row + c * 32 - row0);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    if ((cm >> j) & 1u) {
-                        const uint32_t half_delta =
-                            (uint32_t)(a.x - __float2int_rn(__uint_as_float(v[j])));
-                        staging[sc * MMA_M + m] = (half_delta << LOCAL_BITS) | (gbase + (uint32_t)j);
-                        ++sc;
+                for (int i = 0; i < 8; ++i) {
+                    if (!__any_sync(0xffffffffu, sm[i] > thr && 4 * i < lim)) continue;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = 4 * i + jj;
+                        const float dv = __uint_as_float(v[j]);
+                        if (dv > thr && j < lim) {
+                            const uint32_t half_delta = (uint32_t)(a.x - __float2int_rn(dv));
+                            staging[sc * MMA_M + m] = (half_delta << LOCAL_BITS) | (gbase + (uint32_t)j);
+                            ++sc;
+                        }
                     }
                 }
             };
@@ -480,7 +652,11 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 if (c + 2 < MMA_N / 32) tmem_wait_ld(va);
             }
             tc_fence_before();
-            mbar_arrive(&acc_empty[b]);
+            __syncwarp();
+            if (lane == 0) {
+                if constexpr (CG == 1) mbar_arrive(&acc_empty[b]);
+                else mbar_arrive_cluster(b ? acc_empty1 : acc_empty0);
+            }
         }
         if (!ok) break;
         flush();
@@ -508,9 +684,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                           (unsigned long long)last);
         }
         }  // item
-        if (!ok) {
-            report(a.status, EVP_ERR_TIMEOUT);
-            *(volatile int*)abort_flag = 1;
+        if (!ok && lane == 0) {
+            if (!*(volatile int*)abort_flag) report(a.status, EVP_ERR_TIMEOUT);
+            raise_abort();
         }
         __syncwarp();
         if (warp == 2 && lane == 0) *reinterpret_cast<volatile int*>(epi_done) = 1;
@@ -536,7 +712,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 for (int j = 0; j < MMA_M / 32; ++j) best[j] = 0xFFFFFFFFu;
                 seen = item;
             }
-            const int qt = item % a.qtiles;
+            const int qt = item_of(item).qt;
 #pragma unroll 1
             for (int j = 0; j < MMA_M / 32; ++j) {
                 const int mm = j * 32 + lane;
@@ -571,11 +747,24 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
     tc_fence_before();
     __syncthreads();
+    if (*(volatile int*)abort_flag && threadIdx.x == 0) {
+        // after an abort, copies and MMAs already issued into this CTA's
+        // shared memory may still be in flight: give them time to land
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 5000000ull) __nanosleep(10000);
+    }
+    __syncthreads();
+    if constexpr (CG == 2) cluster_sync_all();  // no arrivals into the peer remain
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"(TMEM_COLS)
-                     : "memory");
+        if constexpr (CG == 1)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"(TMEM_COLS)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"(TMEM_COLS)
+                         : "memory");
     }
 }
 
@@ -634,17 +823,57 @@ int mma_active_queries(int k) {
     return qa;
 }
 
+// CTA pairs the device can keep resident at once; 0 (single CTAs) unless
+// EVP_MMA_CTA_PAIR=1 is set in the environment.
+int mma_pair_workers() {
+    const char* env = std::getenv("EVP_MMA_CTA_PAIR");
+    if (!env || env[0] != '1') return 0;
+    static int cached[64];
+    static bool known[64] = {false};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (!known[dev]) {
+        int n = 0;
+        if (cudaFuncSetAttribute(scan_mma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MmaCfg<2>::SMEM_BYTES) == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(2 * (unsigned)num_sms());
+            cfg.blockDim = dim3(NUM_THREADS);
+            cfg.dynamicSmemBytes = MmaCfg<2>::SMEM_BYTES;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if (cudaOccupancyMaxActiveClusters(&n, scan_mma_kernel<2>, &cfg) != cudaSuccess) n = 0;
+        }
+        cudaGetLastError();
+        cached[dev] = std::max(0, n);
+        known[dev] = true;
+    }
+    return cached[dev];
+}
+
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
     MmaPlan p{};
     p.kp = mma_kp(d);
     p.qa = mma_active_queries(k);
     p.qtiles = (int)((nq + p.qa - 1) / p.qa);
+    const int pairs = mma_pair_workers();
+    p.cg = pairs > 0 ? 2 : 1;
+    p.workers = pairs > 0 ? pairs : num_sms();
+    const int units = (p.qtiles + p.cg - 1) / p.cg;
     const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
     const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
-    // qtiles * slices a multiple of the SM count (whole waves of the
+    // units * slices a multiple of the resident workers (whole waves of the
     // persistent grid), at least min_slices, at most one slice per tile
-    const int64_t sms = num_sms();
-    int64_t g = sms, b = std::max(1, p.qtiles);
+    const int64_t sms = p.workers;
+    int64_t g = sms, b = std::max(1, units);
     while (b) {
         const int64_t r = g % b;
         g = b;
@@ -713,7 +942,7 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     cuuint64_t gdimB[2] = {(cuuint64_t)p.kp, (cuuint64_t)ns};
     cuuint64_t gstride[1] = {(cuuint64_t)p.kp};
     cuuint32_t boxA[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)MMA_M};
-    cuuint32_t boxB[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)MMA_N};
+    cuuint32_t boxB[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)(MMA_N / p.cg)};
     cuuint32_t es[2] = {1, 1};
     if (enc(&tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, A8, gdimA, gstride, boxA, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -741,14 +970,31 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.minhalf = minhalf;
     args.hist_bins = hist_bins;
     args.status = status;
-    if (cudaFuncSetAttribute(scan_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)SMEM_BYTES) != cudaSuccess)
-        return EVP_ERR_CUDA;
-    {
+    const int items = (p.qtiles + p.cg - 1) / p.cg * p.nslices;
+    if (p.cg == 1) {
+        if (cudaFuncSetAttribute(scan_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MmaCfg<1>::SMEM_BYTES) != cudaSuccess)
+            return EVP_ERR_CUDA;
         TimedLaunch timer("scan_mma", stream);
-        const int items = p.qtiles * p.nslices;
-        scan_mma_kernel<<<std::min(items, num_sms()), NUM_THREADS, SMEM_BYTES, stream>>>(tmA, tmB,
-                                                                                        args);
+        scan_mma_kernel<1><<<std::min(items, p.workers), NUM_THREADS, MmaCfg<1>::SMEM_BYTES,
+                             stream>>>(tmA, tmB, args);
+    } else {
+        // attribute already set by mma_pair_workers
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * (unsigned)std::min(items, p.workers));
+        cfg.blockDim = dim3(NUM_THREADS);
+        cfg.dynamicSmemBytes = MmaCfg<2>::SMEM_BYTES;
+        cfg.stream = stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        TimedLaunch timer("scan_mma", stream);
+        if (cudaLaunchKernelEx(&cfg, scan_mma_kernel<2>, tmA, tmB, args) != cudaSuccess)
+            return EVP_ERR_CUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
     return launch_final_merge(lists, meta, tau, nq, p.nslices, k, ids, dist, stream);

@@ -153,3 +153,24 @@ def test_argument_errors(evp_lib, dev):
                                     out.data_ptr(), out.data_ptr(), ws.data_ptr(), 256, None,
                                     torch.cuda.current_stream().cuda_stream)
     assert rc == evp_lib.EVP_ERR_NO_MEMORY
+
+
+@pytest.mark.parametrize("pair", ["0", "1"])
+@pytest.mark.parametrize("nq,ns,d,k", [(1, 3001, 384, 10),      # one tile, the pair's second CTA idle
+                                       (129, 70_001, 256, 20),  # two tiles: one pair
+                                       (300, 12_000, 768, 10),  # three tiles: odd count
+                                       (513, 4_001, 1024, 100),
+                                       (100, 40_000, 128, 600),  # qa = 16 queries per tile
+                                       (40, 5_000, 64, 1024)])
+def test_tensor_path_cta_pair_and_single(evp_lib, dev, monkeypatch, pair, nq, ns, d, k):
+    """The tensor-core scan with CTA pairs (M = 256 per instruction, each CTA
+    staging half of the database tile) and with single CTAs gives the oracle's
+    ids and Delta bit for bit."""
+    monkeypatch.setenv("EVP_MMA_CTA_PAIR", pair)
+    x = oracle.default_x(d)
+    Vs = synth.ternary_random(ns, d, x, stream=900 + d)
+    Vq = synth.ternary_random(nq, d, x, stream=950 + d)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path=2)
+    oi, od = oracle.knn(Vq, Vs, k)
+    np.testing.assert_array_equal(dist, od)
+    np.testing.assert_array_equal(ids, oi)
