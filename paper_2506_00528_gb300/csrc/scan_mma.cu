@@ -63,6 +63,7 @@ constexpr int EPI_WARPS = 4;
 constexpr int A_STAGE_BYTES = MMA_M * KCHUNK;
 constexpr int HEAP_BYTES = HEAP_SLOTS * 4;
 constexpr int STAGE_SLOTS = 32;                     // per-thread candidate staging
+constexpr int FLUSH_AT = 8;   // staged keys that trigger a flush at the end of a tile
 constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
@@ -205,9 +206,12 @@ __device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t rank) {
     return r;
 }
 
+// Arrival on a barrier of either CTA of the pair.  Release at CTA scope
+// (the default) suffices: the only data it publishes are TMEM reads, which
+// tcgen05.fence::before_thread_sync orders; a cluster-scope release would
+// wait for every outstanding memory operation of the thread.
 __device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
-                 : "memory");
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster) : "memory");
 }
 
 __device__ __forceinline__ void st_cluster_u32(uint32_t addr_cluster, uint32_t v) {
@@ -274,22 +278,6 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
           "+r"(v[31])
         :
         : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-        "[%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Max-heap of u32 keys, element i of thread m at h[i * qa + m] (qa = active
@@ -657,6 +645,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 if constexpr (CG == 1) mbar_arrive(&acc_empty[b]);
                 else mbar_arrive_cluster(b ? acc_empty1 : acc_empty0);
             }
+            // heap updates run after the accumulator is released, overlapping
+            // the next tile's MMAs
+            if (__any_sync(0xffffffffu, sc > FLUSH_AT)) flush();
         }
         if (!ok) break;
         flush();
@@ -823,11 +814,11 @@ int mma_active_queries(int k) {
     return qa;
 }
 
-// CTA pairs the device can keep resident at once; 0 (single CTAs) unless
-// EVP_MMA_CTA_PAIR=1 is set in the environment.
+// CTA pairs the device can keep resident at once (0: pairs unavailable, or
+// single CTAs requested with EVP_MMA_CTA_PAIR=0 in the environment).
 int mma_pair_workers() {
     const char* env = std::getenv("EVP_MMA_CTA_PAIR");
-    if (!env || env[0] != '1') return 0;
+    if (env && env[0] == '0') return 0;
     static int cached[64];
     static bool known[64] = {false};
     int dev = 0;
