@@ -166,6 +166,8 @@ struct ScanPlan {
     int qb;             // queries per scan pass
     int groups;         // passes
     size_t list_bytes;  // per-pass list storage
+    size_t meta_bytes;  // per-pass list lengths
+    size_t hist_bytes;  // union-bound histograms and minima
     size_t ws_bytes;    // total workspace
 };
 ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k);

@@ -23,11 +23,16 @@
 //     is appended to that query's candidate buffer; buffers are merged
 //     (bitonic sort + merge-path) into a per-(query, slice) sorted list of
 //     the k best, kept in the workspace;
-//   * once a slice's list is full, its k-th key is folded into a global
-//     per-query threshold with atomicMin, and every CTA filters with the
-//     smaller of its own and the global threshold.  Any key above the
-//     global threshold has k better keys in some slice, so it cannot be in
-//     the answer.
+//   * every appended key is also counted in a per-query Delta/2 histogram
+//     in the workspace (each row is appended at most once); after a merge,
+//     the smallest T with count(Delta/2 <= T) >= k over all slices' keys
+//     bounds the answer (those keys are real rows), and so does a full
+//     slice list's k-th key.  Both are folded into a global per-query
+//     threshold with atomicMin, and every CTA filters with the smaller of
+//     its own and the global threshold;
+//   * a merge is done by a team of warps per query (all warps of the CTA
+//     take part whatever the pass size): bitonic sort, merge path, and the
+//     histogram scan for the bound.
 // A second kernel merges, per query, the slice lists' keys that do not
 // exceed the final global threshold into the k best.
 #include "evp_internal.cuh"
@@ -62,6 +67,9 @@ struct ScanArgs {
     uint64_t* lists;     // [QB_MAX][nslices][2][k]
     int32_t* meta;       // [QB_MAX][nslices][2]: (length, current buffer)
     uint64_t* tau_global;  // [QB_MAX]
+    uint32_t* hist;      // [QB_MAX][hist_bins]: Delta/2 of every key any slice appended
+    uint32_t* minhalf;   // [QB_MAX]: smallest Delta/2 any slice appended
+    int hist_bins;       // 2x + 1
     int32_t* status;
 };
 
@@ -92,6 +100,93 @@ __device__ inline int next_pow2(int v) {
     int p = 32;
     while (p < v) p <<= 1;
     return p;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// Ascending bitonic sort of buf[0, P) (P a power of two) by a team of TT
+// threads (t = thread index in the team) that synchronises with `sync`.
+template <typename Sync>
+__device__ __forceinline__ void team_bitonic_sort(uint64_t* buf, int P, int t, int TT, Sync& sync) {
+    for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = t; i < P; i += TT) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t x0 = buf[i], x1 = buf[ixj];
+                    const bool up = (i & kk) == 0;
+                    if ((x0 > x1) == up) {
+                        buf[i] = x1;
+                        buf[ixj] = x0;
+                    }
+                }
+            }
+            sync();
+        }
+    }
+}
+
+// The k smallest of two ascending lists L[0, nL) and C[0, nc) (no key in
+// both) into out[0, min(nL + nc, k)), by merge path: each key's output rank
+// is its own index plus the number of smaller keys in the other list.
+__device__ __forceinline__ int team_merge_topk(const uint64_t* L, int nL, const uint64_t* C, int nc,
+                                               uint64_t* out, int k, int t, int TT) {
+    for (int i = t; i < nL; i += TT) {
+        const uint64_t key = L[i];
+        const int r = i + lower_bound_u64(C, nc, key);
+        if (r < k) out[r] = key;
+    }
+    for (int j = t; j < nc; j += TT) {
+        const uint64_t key = C[j];
+        const int r = j + lower_bound_u64(L, nL, key);
+        if (r < k) out[r] = key;
+    }
+    const int total = nL + nc;
+    return total < k ? total : k;
+}
+
+// The smallest bin T with sum(hist[0..T]) >= k, scanning up from the
+// smallest non-empty bin; 0xFFFFFFFF if fewer than k keys are counted.
+// Team-wide (every thread gets the result); `scratch` holds TT/32 + 2 words.
+template <typename Sync>
+__device__ __forceinline__ uint32_t team_kth_bin(const uint32_t* hist, const uint32_t* minhalf,
+                                                 int bins, uint32_t k, uint32_t* scratch, int t,
+                                                 int TT, Sync& sync) {
+    const int nw = TT / 32, wt = t >> 5, ln = t & 31;
+    if (t == 0) {
+        scratch[nw] = __ldcg(minhalf);
+        scratch[nw + 1] = 0xFFFFFFFFu;
+    }
+    sync();
+    const uint32_t lo = scratch[nw];
+    uint32_t before = 0, T = 0xFFFFFFFFu;
+    for (uint32_t h0 = lo; h0 < (uint32_t)bins; h0 += (uint32_t)TT) {
+        const uint32_t h = h0 + (uint32_t)t;
+        const uint32_t c = h < (uint32_t)bins ? __ldcg(&hist[h]) : 0u;
+        uint32_t sum = c;  // inclusive scan over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n = __shfl_up_sync(0xffffffffu, sum, o);
+            if (ln >= o) sum += n;
+        }
+        if (ln == 31) scratch[wt] = sum;
+        sync();
+        uint32_t off = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t v = scratch[w];
+            if (w < wt) off += v;
+            total += v;
+        }
+        sum += off;
+        if (c > 0 && before + sum >= k && before + sum - c < k) scratch[nw + 1] = h;
+        sync();
+        T = scratch[nw + 1];
+        before += total;
+        if (T != 0xFFFFFFFFu || before >= k) break;
+    }
+    return T;
 }
 
 // TPR threads share a row (each takes QB / TPR of the pass's queries), so a
@@ -193,6 +288,9 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
                     if (key < tau[gq]) {
                         const int pos = atomicAdd(&cnt[gq], 1);
                         cand[gq * CAND_CAP + pos] = key;
+                        // each row is appended at most once: count it for the union bound
+                        atomicAdd(&a.hist[gq * a.hist_bins + (delta >> 1)], 1u);
+                        atomicMin(&a.minhalf[gq], delta >> 1);
                     }
                 }
             }
@@ -213,32 +311,52 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         }
         if (mask) {
             __syncthreads();  // every thread has read cnt before it changes
-            for (int q = warp; q < QB; q += NT / 32) {
+            // A team of TEAM warps per query; the pass's queries merge side
+            // by side (all warps of the CTA take part, whatever the pass size).
+            constexpr int TEAM = NT / 32 >= QB ? NT / 32 / QB : 1;
+            constexpr int TT = TEAM * 32;
+            const int team = warp / TEAM, t = tid - team * TT;
+            auto sync = [&]() {
+                if constexpr (TEAM == 1) __syncwarp();
+                else named_barrier(1 + team, TT);
+            };
+            for (int q = team; q < QB; q += NT / TT) {
                 if (!((mask >> q) & 1)) continue;
                 uint64_t* C = cand + q * CAND_CAP;
                 const int nc = cnt[q];
                 const int P = next_pow2(nc);
-                for (int i = nc + lane; i < P; i += 32) C[i] = KEY_NONE;
-                __syncwarp();
-                warp_bitonic_sort(C, P);
+                for (int i = nc + t; i < P; i += TT) C[i] = KEY_NONE;
+                sync();
+                team_bitonic_sort(C, P, t, TT, sync);
                 uint64_t* base = a.lists + ((int64_t)q * nslices + slice) * 2 * k;
                 const int c0 = cur[q];
-                const int nl = warp_merge_topk(base + c0 * k, len[q], C, nc, base + (c0 ^ 1) * k, k);
-                if (lane == 0) {
+                const int nl = team_merge_topk(base + c0 * k, len[q], C, nc, base + (c0 ^ 1) * k, k,
+                                               t, TT);
+                sync();  // the new list is complete; C is free
+                uint64_t t_new = KEY_NONE;
+                if (nl == k) t_new = base[(c0 ^ 1) * k + k - 1];
+                if (!last) {
+                    // union bound: the smallest T with count(Delta/2 <= T) >= k
+                    // over the keys all slices of the query have appended
+                    const uint32_t T = team_kth_bin(a.hist + (int64_t)q * a.hist_bins,
+                                                    a.minhalf + q, a.hist_bins, (uint32_t)k,
+                                                    reinterpret_cast<uint32_t*>(C), t, TT, sync);
+                    if (T != 0xFFFFFFFFu) t_new = min(t_new, (uint64_t)(2u * T + 1u) << 32);
+                }
+                if (t == 0) {
                     cur[q] = c0 ^ 1;
                     len[q] = nl;
                     cnt[q] = 0;
-                    uint64_t t = tau[q];
-                    if (nl == k) {
-                        const uint64_t kth = base[(c0 ^ 1) * k + k - 1];
+                    uint64_t tq = min(tau[q], t_new);
+                    if (t_new != KEY_NONE) {
                         const unsigned long long old =
                             atomicMin(reinterpret_cast<unsigned long long*>(&a.tau_global[q]),
-                                      (unsigned long long)kth);
-                        t = min(t, min(kth, (uint64_t)old));
+                                      (unsigned long long)t_new);
+                        tq = min(tq, (uint64_t)old);
                     } else {
-                        t = min(t, *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
+                        tq = min(tq, *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
                     }
-                    tau[q] = t;
+                    tau[q] = tq;
                 }
             }
             __syncthreads();
@@ -266,8 +384,14 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
     }
 }
 
-__global__ void init_tau_kernel(uint64_t* tau_global) {
-    if (threadIdx.x < QB_MAX) tau_global[threadIdx.x] = KEY_NONE;
+// Per pass: thresholds, histograms and minima of the union bound start empty.
+__global__ void init_tau_kernel(uint64_t* tau_global, uint32_t* hist, int hist_words,
+                                uint32_t* minhalf) {
+    if (threadIdx.x < QB_MAX) {
+        tau_global[threadIdx.x] = KEY_NONE;
+        minhalf[threadIdx.x] = 0xFFFFFFFFu;
+    }
+    for (int i = threadIdx.x; i < hist_words; i += blockDim.x) hist[i] = 0u;
 }
 
 // Per query (one CTA): the k smallest keys of the union of the per-slice
@@ -477,16 +601,16 @@ ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k) {
     p.qb = (int)std::min<int64_t>(QB_MAX, std::max<int64_t>(1, nq));
     p.groups = (int)((nq + QB_MAX - 1) / QB_MAX);
     p.list_bytes = align_up((size_t)QB_MAX * p.nslices * 2 * k * 8, 256);
-    const size_t meta_bytes = align_up((size_t)QB_MAX * p.nslices * 2 * 4, 256);
-    p.ws_bytes = p.list_bytes + meta_bytes + 256;
-    (void)d;
+    p.meta_bytes = align_up((size_t)QB_MAX * p.nslices * 2 * 4, 256);
+    // union-bound histograms: Delta/2 in [0, 2x], x <= d
+    p.hist_bytes = align_up((size_t)QB_MAX * (2 * d + 1) * 4, 256) + 256;
+    p.ws_bytes = p.list_bytes + p.meta_bytes + p.hist_bytes + 256;
     return p;
 }
 
 int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
                      int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                      int32_t* status, cudaStream_t stream) {
-    (void)x;
     const int W = (d + 63) / 64;
     const ScanPlan p = plan_popc_scan(nq, ns, d, k);
     if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
@@ -517,6 +641,9 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
     a.lists = reinterpret_cast<uint64_t*>(wsb);
     a.meta = reinterpret_cast<int32_t*>(wsb + p.list_bytes);
     a.tau_global = reinterpret_cast<uint64_t*>(wsb + p.ws_bytes - 256);
+    a.hist = reinterpret_cast<uint32_t*>(wsb + p.list_bytes + p.meta_bytes);
+    a.minhalf = reinterpret_cast<uint32_t*>(wsb + p.list_bytes + p.meta_bytes + p.hist_bytes - 256);
+    a.hist_bins = 2 * x + 1;
     a.status = status;
 
 
@@ -530,7 +657,8 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
         const SmemLayout L = smem_layout(W, a.stages, qb);
         {
             TimedLaunch timer("scan_init", stream);
-            init_tau_kernel<<<1, 32, 0, stream>>>(a.tau_global);
+            init_tau_kernel<<<1, 256, 0, stream>>>(a.tau_global, a.hist, QB_MAX * a.hist_bins,
+                                                  a.minhalf);
         }
         cudaError_t e;
         if (nqg <= 1) e = launch_scan<1, 1>(tmap, a, p.nslices, L.total, stream);
