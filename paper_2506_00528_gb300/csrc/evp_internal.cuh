@@ -179,6 +179,7 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
 // Per-query merge of per-(query, slice) sorted key lists ([nq][nslices][2][k]
 // with meta [nq][nslices] = (length, buffer)) into the k best.
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
+                           const uint32_t* hist, const uint32_t* minhalf, int hist_bins,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
                            cudaStream_t stream);
 

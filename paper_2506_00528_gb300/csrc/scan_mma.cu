@@ -988,7 +988,8 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
             return EVP_ERR_CUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
-    return launch_final_merge(lists, meta, tau, nq, p.nslices, k, ids, dist, stream);
+    return launch_final_merge(lists, meta, tau, hist, minhalf, hist_bins, nq, p.nslices, k, ids,
+                              dist, stream);
 }
 
 }  // namespace evp

@@ -51,7 +51,8 @@ constexpr int MAX_STAGES = 4;
 constexpr int SMEM_BUDGET = 225 * 1024;
 constexpr int FM_THREADS = 256;                 // final merge: one CTA per query
 constexpr int FM_MAX_SLICES = 1024;             // slice lists per query in the final merge
-constexpr int FM_OUT_BYTES = EVP_MAX_K * 8;     // sorted output keys
+constexpr int FM_GATHER = 2048;                 // keys at or below the threshold hint merged directly
+constexpr int FM_OUT_BYTES = (EVP_MAX_K > FM_GATHER ? EVP_MAX_K : FM_GATHER) * 8;  // sort buffer
 constexpr int FM_STAGE_BYTES = 160 * 1024;      // lists staged in shared memory up to this size
 
 struct ScanArgs {
@@ -395,11 +396,13 @@ __global__ void init_tau_kernel(uint64_t* tau_global, uint32_t* hist, int hist_w
 }
 
 // Per query (one CTA): the k smallest keys of the union of the per-slice
-// sorted lists.  The k-th smallest key T of the union is found bit by bit
-// from the top (the smallest T with count(key <= T) >= k), each count being
-// a sum of per-list binary searches; then every list contributes its prefix
-// of keys <= T (exactly k keys in all, keys being distinct) and those k keys
-// are sorted.  Lists are staged in shared memory when they fit.
+// sorted lists.  With the scan's final threshold as a hint, the keys at or
+// below it (at least k of them; usually a few more) are gathered and sorted
+// directly.  Otherwise the k-th smallest key T of the union is found bit by
+// bit from the top (the smallest T with count(key <= T) >= k), each count
+// being a sum of per-list binary searches, with the lists staged in shared
+// memory when they fit; then every list contributes its prefix of keys
+// <= T (exactly k keys in all, keys being distinct) and those are sorted.
 __device__ __forceinline__ int upper_bound_u64(const uint64_t* a, int n, uint64_t key) {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -412,12 +415,14 @@ __device__ __forceinline__ int upper_bound_u64(const uint64_t* a, int n, uint64_
 
 __global__ void __launch_bounds__(FM_THREADS)
 final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
-                   int nslices, int k, int key_bits, int stage_lists,
-                   int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
+                   const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
+                   const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k,
+                   int key_bits, int stage_lists, int64_t* __restrict__ ids,
+                   int32_t* __restrict__ dist) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int red[FM_THREADS / 32];
     __shared__ int total_s;
-    uint64_t* out = reinterpret_cast<uint64_t*>(smem);           // next_pow2(k) keys
+    uint64_t* out = reinterpret_cast<uint64_t*>(smem);           // sort buffer
     int* lens = reinterpret_cast<int*>(smem + FM_OUT_BYTES);     // nslices
     int* offs = lens + FM_MAX_SLICES;                            // nslices
     uint64_t* staged = reinterpret_cast<uint64_t*>(smem + FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4);
@@ -427,16 +432,10 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
 
     for (int s = tid; s < nslices; s += FM_THREADS) lens[s] = meta[(qbase + s) * 2];
     __syncthreads();
-    if (stage_lists) {
-        for (int64_t e = tid; e < (int64_t)nslices * k; e += FM_THREADS) {
-            const int s = (int)(e / k), i = (int)(e - (int64_t)s * k);
-            if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k + i];
-        }
-        __syncthreads();
-    }
+    bool staged_now = false;
     auto list_ptr = [&](int s) -> const uint64_t* {
-        return stage_lists ? staged + (int64_t)s * k
-                           : lists + ((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k;
+        return staged_now ? staged + (int64_t)s * k
+                          : lists + ((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k;
     };
     auto count_le = [&](uint64_t v) -> int {
         int c = 0;
@@ -450,13 +449,65 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
         __syncthreads();
         return t;
     };
-    // smallest T with count(key <= T) >= k
-    uint64_t T = 0;
-    for (int b = key_bits - 1; b >= 0; --b) {
-        const uint64_t lowmax = T | ((1ull << b) - 1ull);
-        if (count_le(lowmax) < k) T |= 1ull << b;
+    // The scan's final threshold, when given, bounds the k-th smallest key
+    // from above (at least k keys of the lists lie at or below it), and so
+    // does the smallest T with count(Delta/2 <= T) >= k over the scan's
+    // now complete histogram of listed keys; if few keys lie at or below the
+    // tighter of the two, they are merged directly.
+    uint64_t T = tau ? tau[q] : KEY_NONE;
+    if (hist) {
+        const uint32_t* H = hist + q * (int64_t)hist_bins;
+        const uint32_t lo = minhalf[q];
+        __shared__ uint32_t kth_bin;
+        if (tid == 0) kth_bin = 0xFFFFFFFFu;
+        __syncthreads();
+        uint32_t before = 0;
+        for (uint32_t h0 = lo; h0 < (uint32_t)hist_bins; h0 += FM_THREADS) {
+            const uint32_t h = h0 + (uint32_t)tid;
+            const uint32_t c = h < (uint32_t)hist_bins ? H[h] : 0u;
+            uint32_t sum = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t nb = __shfl_up_sync(0xffffffffu, sum, o);
+                if (lane >= o) sum += nb;
+            }
+            if (lane == 31) red[warp] = (int)sum;
+            __syncthreads();
+            uint32_t off = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < FM_THREADS / 32; ++w) {
+                const uint32_t v = (uint32_t)red[w];
+                if (w < warp) off += v;
+                total += v;
+            }
+            sum += off;
+            if (c > 0 && before + sum >= (uint32_t)k && before + sum - c < (uint32_t)k) kth_bin = h;
+            __syncthreads();
+            before += total;
+            if (kth_bin != 0xFFFFFFFFu || before >= (uint32_t)k) break;
+        }
+        if (kth_bin != 0xFFFFFFFFu) T = min(T, (uint64_t)(2u * kth_bin + 1u) << 32);
     }
-    // each list's prefix of keys <= T, gathered at exclusive-scan offsets
+    int m = T != KEY_NONE ? count_le(T) : FM_GATHER + 1;
+    if (m < k || m > FM_GATHER) {
+        if (stage_lists) {
+            for (int64_t e = tid; e < (int64_t)nslices * k; e += FM_THREADS) {
+                const int s = (int)(e / k), i = (int)(e - (int64_t)s * k);
+                if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k + i];
+            }
+            __syncthreads();
+            staged_now = true;
+        }
+        // smallest T with count(key <= T) >= k, built bit by bit
+        T = 0;
+        for (int b = key_bits - 1; b >= 0; --b) {
+            const uint64_t lowmax = T | ((1ull << b) - 1ull);
+            if (count_le(lowmax) < k) T |= 1ull << b;
+        }
+        m = k;
+    }
+    // each list's prefix of keys <= T (m keys in all), gathered at
+    // exclusive-scan offsets, then sorted
     for (int s = tid; s < nslices; s += FM_THREADS) offs[s] = upper_bound_u64(list_ptr(s), lens[s], T);
     __syncthreads();
     if (tid == 0) {
@@ -469,16 +520,17 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
         total_s = run;
     }
     __syncthreads();
-    const int n = min(total_s, k);
+    const int cap = max(m, k);
+    const int n = min(total_s, min(cap, k));
     int P = 2;
-    while (P < k) P <<= 1;
+    while (P < cap) P <<= 1;
     for (int i = tid; i < P; i += FM_THREADS) out[i] = KEY_NONE;
     __syncthreads();
     for (int s = tid; s < nslices; s += FM_THREADS) {
         const uint64_t* L = list_ptr(s);
         const int o = offs[s];
         const int c = upper_bound_u64(L, lens[s], T);
-        for (int i = 0; i < c && o + i < k; ++i) out[o + i] = L[i];
+        for (int i = 0; i < c && o + i < cap; ++i) out[o + i] = L[i];
     }
     __syncthreads();
     for (int kk = 2; kk <= P; kk <<= 1) {
@@ -553,9 +605,9 @@ __global__ void pack_lists_kernel(const int64_t* __restrict__ ids, const int32_t
 }
 
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
+                           const uint32_t* hist, const uint32_t* minhalf, int hist_bins,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
                            cudaStream_t stream) {
-    (void)tau;
     if (nq <= 0) return EVP_OK;
     if (nslices > FM_MAX_SLICES) return EVP_ERR_UNSUPPORTED;
     const size_t list_bytes = (size_t)nslices * k * 8;
@@ -567,8 +619,8 @@ int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uin
     // keys are (Delta << 32 | row) with Delta <= 4 * EVP_MAX_D_SCAN
     const int key_bits = 32 + 13;
     TimedLaunch timer("final_merge", stream);
-    final_merge_kernel<<<(unsigned)nq, FM_THREADS, smem, stream>>>(lists, meta, nslices, k,
-                                                                   key_bits, stage, ids, dist);
+    final_merge_kernel<<<(unsigned)nq, FM_THREADS, smem, stream>>>(
+        lists, meta, tau, hist, minhalf, hist_bins, nslices, k, key_bits, stage, ids, dist);
     return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 
@@ -590,7 +642,8 @@ int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int 
             ids, dist, nq, nlists, k, lists, meta, status);
     }
     if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
-    return launch_final_merge(lists, meta, nullptr, nq, nlists, k, out_ids, out_dist, stream);
+    return launch_final_merge(lists, meta, nullptr, nullptr, nullptr, 0, nq, nlists, k, out_ids,
+                              out_dist, stream);
 }
 
 ScanPlan plan_popc_scan(int64_t nq, int64_t ns, int d, int k) {
@@ -667,7 +720,8 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
         else if (nqg <= 8) e = launch_scan<8, 2>(tmap, a, p.nslices, L.total, stream);
         else e = launch_scan<16, 2>(tmap, a, p.nslices, L.total, stream);
         if (e != cudaSuccess) return EVP_ERR_CUDA;
-        const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, nqg, p.nslices, k,
+        const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, a.hist, a.minhalf,
+                                              a.hist_bins, nqg, p.nslices, k,
                                               ids + q0 * k, dist + q0 * k, stream);
         if (rc != EVP_OK) return rc;
     }
