@@ -66,6 +66,35 @@ def load_peaks():
 # maximum SM clock, for the integer-pipe roofline of the popcount scan.
 POPC_PER_CLK_PER_SM = 16
 
+# DRAM traffic per launch of the dominant kernel (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum, one capture of this bench's own command), keyed by
+# (kernel, rows, d, queries per step, scan k).  Each entry carries the
+# SHA-256 of the kernel sources it was measured on and is reported only
+# while those sources are unchanged; otherwise the traffic is null.
+KERNEL_SOURCES = {
+    "scan_mma": ["paper_2506_00528_gb300/csrc/scan_mma.cu",
+                 "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
+    "scan_popc": ["paper_2506_00528_gb300/csrc/scan_popc.cu",
+                  "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
+}
+MEASURED_TRAFFIC = {}
+
+
+def kernel_sources_sha(kernel: str) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, n: int, d: int, batch: int, k_scan: int):
+    e = MEASURED_TRAFFIC.get((kernel, n, d, batch, k_scan))
+    if e is None or e["sources_sha256"] != kernel_sources_sha(kernel):
+        return None
+    return e["bytes"]
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
@@ -449,7 +478,8 @@ def main():
         roofline = {
             "kernel": "scan_mma", "bound": "tensor",
             "achieved": flops / (avg / 1e3) / 1e12, "peak": fp8_peak, "unit": "TFLOP/s",
-            "frac": flops / (avg / 1e3) / 1e12 / fp8_peak, "traffic": None,
+            "frac": flops / (avg / 1e3) / 1e12 / fp8_peak,
+            "traffic": measured_traffic("scan_mma", n, d, B, a.shortlist),
             "peak_source": f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s ({peak_src})",
             "launches": n_mma, "avg_ms": avg,
         }
@@ -472,7 +502,7 @@ def main():
             "unit": "GB/s" if hbm_bound else "Tpopc/s",
             "frac": (bytes_per_launch / (avg / 1e3) / 1e9 / hbm_peak) if hbm_bound
             else (popc_per_launch / (avg / 1e3)) / popc_peak,
-            "traffic": None,
+            "traffic": measured_traffic("scan_popc", n, d, B, a.shortlist),
             "hbm_achieved_gbs": bytes_per_launch / (avg / 1e3) / 1e9,
             "popc_achieved_tops": popc_per_launch / (avg / 1e3) / 1e12,
             "peak_source": f"POPC 16/clk/SM (probe) x {sm_count} SMs x 2070 MHz; HBM {peak_src}",

@@ -91,7 +91,7 @@ __host__ __device__ inline SmemLayout smem_layout(int W, int stages, int qb) {
     L.cand_off = L.qv_off + align_up((size_t)QB_MAX * W * 16, 128);
     L.tau_off = L.cand_off + (size_t)qb * CAND_CAP * 8;
     L.cnt_off = L.tau_off + QB_MAX * 8;
-    L.bar_off = L.cnt_off + align_up(3 * QB_MAX * 4, 8);
+    L.bar_off = L.cnt_off + align_up(4 * QB_MAX * 4, 8);
     L.flag_off = L.bar_off + MAX_STAGES * 8;
     L.total = L.flag_off + 16;
     return L;
@@ -207,6 +207,7 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
     int* cnt = reinterpret_cast<int*>(smem + L.cnt_off);
     int* len = cnt + QB_MAX;
     int* cur = len + QB_MAX;
+    uint32_t* lmin = reinterpret_cast<uint32_t*>(cur + QB_MAX);  // smallest Delta/2 this CTA appended
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     int* abort_flag = reinterpret_cast<int*>(smem + L.flag_off);
 
@@ -239,6 +240,7 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         cnt[tid] = 0;
         len[tid] = 0;
         cur[tid] = 0;
+        lmin[tid] = 0xFFFFFFFFu;
     }
     __syncthreads();
     if (tid == 0) {
@@ -287,11 +289,23 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
                     const uint32_t delta = (uint32_t)(acc_one[q] + 4 * acc_opp[q]);
                     const uint64_t key = ((uint64_t)delta << 32) | (uint64_t)row;
                     if (key < tau[gq]) {
-                        const int pos = atomicAdd(&cnt[gq], 1);
-                        cand[gq * CAND_CAP + pos] = key;
+                        // warp-aggregated: one slot reservation and one
+                        // minimum per warp and query
+                        const unsigned am = __activemask();
+                        const int leader = __ffs(am) - 1;
+                        const int rank = __popc(am & ((1u << lane) - 1u));
+                        int pos0 = 0;
+                        if (lane == leader) pos0 = atomicAdd(&cnt[gq], __popc(am));
+                        pos0 = __shfl_sync(am, pos0, leader);
+                        cand[gq * CAND_CAP + pos0 + rank] = key;
                         // each row is appended at most once: count it for the union bound
-                        atomicAdd(&a.hist[gq * a.hist_bins + (delta >> 1)], 1u);
-                        atomicMin(&a.minhalf[gq], delta >> 1);
+                        const uint32_t h = delta >> 1;
+                        atomicAdd(&a.hist[gq * a.hist_bins + h], 1u);
+                        const uint32_t wmin = __reduce_min_sync(am, h);
+                        if (lane == leader && wmin < lmin[gq]) {
+                            atomicMin(&lmin[gq], wmin);
+                            atomicMin(&a.minhalf[gq], wmin);
+                        }
                     }
                 }
             }
