@@ -193,7 +193,7 @@ __device__ __forceinline__ uint32_t team_kth_bin(const uint32_t* hist, const uin
 // TPR threads share a row (each takes QB / TPR of the pass's queries), so a
 // CTA runs SCAN_ROWS * TPR threads: more warps to hide the popcount and
 // shared-memory latencies than one thread per row would give.
-template <int QB, int TPR>
+template <int QB, int TPR, int WW, bool EXACT>
 __global__ void __launch_bounds__(SCAN_ROWS * TPR, 1)
 scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
     constexpr int NT = SCAN_ROWS * TPR;
@@ -252,77 +252,27 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
         }
     }
 
+    // Per tile: wait for the stage; merge the earlier tiles' candidates if
+    // a buffer could overflow (or, after the last tile, all of them); copy
+    // this thread's row into registers and release the stage (its next copy
+    // starts at once, so every stage keeps loading while rows are scored);
+    // then score the row against the pass's queries from registers.
     int it = 0;
-    for (; it < ntl; ++it) {
+    for (;; ++it) {
+        const bool fin = it == ntl;
         const int s = it % a.stages;
-        const uint32_t parity = (uint32_t)((it / a.stages) & 1);
-        if (tid == 0 && !mbar_wait_bounded(&bars[s], parity)) {
+        if (!fin && tid == 0 &&
+            !mbar_wait_bounded(&bars[s], (uint32_t)((it / a.stages) & 1))) {
             report(a.status, EVP_ERR_TIMEOUT);
             *abort_flag = 1;
         }
-        __syncthreads();
+        __syncthreads();  // stage s landed; the earlier tiles' candidates are visible
         if (*abort_flag) break;
-
-        const int64_t row = (tile0 + it) * SCAN_ROWS + rt;
-        if (row < a.ns) {
-            const uint64_t* rp =
-                reinterpret_cast<const uint64_t*>(smem + s * L.stage_bytes) + rt * a.pitch;
-            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qv) + qbase * W;
-            int acc_one[QPT], acc_opp[QPT];
-#pragma unroll
-            for (int q = 0; q < QPT; ++q) acc_one[q] = acc_opp[q] = 0;
-#pragma unroll 2
-            for (int w = 0; w < W; ++w) {
-                const uint64_t sp = rp[w], sn = rp[W + w];
-                const uint64_t sm = sp | sn;
-#pragma unroll
-                for (int q = 0; q < QPT; ++q) {
-                    const ulonglong2 qq = q2[q * W + w];
-                    acc_one[q] += __popcll(qq.x ^ sm);
-                    acc_opp[q] += __popcll(qq.x & sm & (qq.y ^ sn));
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < QPT; ++q) {
-                const int gq = qbase + q;
-                if (gq < a.nqg) {
-                    const uint32_t delta = (uint32_t)(acc_one[q] + 4 * acc_opp[q]);
-                    const uint64_t key = ((uint64_t)delta << 32) | (uint64_t)row;
-                    if (key < tau[gq]) {
-                        // warp-aggregated: one slot reservation and one
-                        // minimum per warp and query
-                        const unsigned am = __activemask();
-                        const int leader = __ffs(am) - 1;
-                        const int rank = __popc(am & ((1u << lane) - 1u));
-                        int pos0 = 0;
-                        if (lane == leader) pos0 = atomicAdd(&cnt[gq], __popc(am));
-                        pos0 = __shfl_sync(am, pos0, leader);
-                        cand[gq * CAND_CAP + pos0 + rank] = key;
-                        // each row is appended at most once: count it for the union bound
-                        const uint32_t h = delta >> 1;
-                        atomicAdd(&a.hist[gq * a.hist_bins + h], 1u);
-                        const uint32_t wmin = __reduce_min_sync(am, h);
-                        if (lane == leader && wmin < lmin[gq]) {
-                            atomicMin(&lmin[gq], wmin);
-                            atomicMin(&a.minhalf[gq], wmin);
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();  // stage s consumed, candidates visible
-        if (tid == 0 && it + a.stages < ntl) {
-            fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[s], tile_bytes);
-            tma_load_2d(smem + s * L.stage_bytes, &tmap, &bars[s], 0,
-                        (int32_t)((tile0 + it + a.stages) * SCAN_ROWS));
-        }
-        const bool last = it == ntl - 1;
         uint32_t mask = 0;
 #pragma unroll
         for (int q = 0; q < QB; ++q) {
             const int c = cnt[q];
-            if (c > MERGE_AT || (last && c > 0)) mask |= 1u << q;
+            if (c > MERGE_AT || (fin && c > 0)) mask |= 1u << q;
         }
         if (mask) {
             __syncthreads();  // every thread has read cnt before it changes
@@ -350,7 +300,7 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
                 sync();  // the new list is complete; C is free
                 uint64_t t_new = KEY_NONE;
                 if (nl == k) t_new = base[(c0 ^ 1) * k + k - 1];
-                if (!last) {
+                if (!fin) {
                     // union bound: the smallest T with count(Delta/2 <= T) >= k
                     // over the keys all slices of the query have appended
                     const uint32_t T = team_kth_bin(a.hist + (int64_t)q * a.hist_bins,
@@ -380,6 +330,86 @@ scan_popc_kernel(const __grid_constant__ CUtensorMap tmap, const ScanArgs a) {
             // warp (thread 0 issues the copies and must not wait on L2)
             const int q = NT - 1 - tid;
             tau[q] = min(tau[q], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
+        }
+        if (fin) break;
+
+        const int64_t row = (tile0 + it) * SCAN_ROWS + rt;
+        const bool valid = row < a.ns;
+        uint64_t rm[WW], rn[WW];  // the row: non-zero mask m and sign sigma per word
+        {
+            const uint64_t* rp =
+                reinterpret_cast<const uint64_t*>(smem + s * L.stage_bytes) + rt * a.pitch;
+            if constexpr (EXACT && WW % 2 == 0) {
+                const ulonglong2* rp2 = reinterpret_cast<const ulonglong2*>(rp);
+#pragma unroll
+                for (int w = 0; w < WW; w += 2) {
+                    const ulonglong2 sp = rp2[w / 2], sn = rp2[(WW + w) / 2];
+                    rm[w] = sp.x | sn.x;
+                    rm[w + 1] = sp.y | sn.y;
+                    rn[w] = sn.x;
+                    rn[w + 1] = sn.y;
+                }
+            } else {
+#pragma unroll
+                for (int w = 0; w < WW; ++w) {
+                    const bool in = EXACT || w < W;
+                    const uint64_t sp = in ? rp[w] : 0ull, sn = in ? rp[W + w] : 0ull;
+                    rm[w] = sp | sn;
+                    rn[w] = sn;
+                }
+            }
+        }
+        __syncthreads();  // every row is in registers: stage s is free
+        if (tid == 0 && it + a.stages < ntl) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[s], tile_bytes);
+            tma_load_2d(smem + s * L.stage_bytes, &tmap, &bars[s], 0,
+                        (int32_t)((tile0 + it + a.stages) * SCAN_ROWS));
+        }
+
+        if (valid) {
+            const ulonglong2* q2 = reinterpret_cast<const ulonglong2*>(qv) + qbase * W;
+            int acc_one[QPT], acc_opp[QPT];
+#pragma unroll
+            for (int q = 0; q < QPT; ++q) acc_one[q] = acc_opp[q] = 0;
+#pragma unroll
+            for (int w = 0; w < WW; ++w) {
+                if (EXACT || w < W) {
+#pragma unroll
+                    for (int q = 0; q < QPT; ++q) {
+                        const ulonglong2 qq = q2[q * W + w];
+                        acc_one[q] += __popcll(qq.x ^ rm[w]);
+                        acc_opp[q] += __popcll(qq.x & rm[w] & (qq.y ^ rn[w]));
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < QPT; ++q) {
+                const int gq = qbase + q;
+                if (gq < a.nqg) {
+                    const uint32_t delta = (uint32_t)(acc_one[q] + 4 * acc_opp[q]);
+                    const uint64_t key = ((uint64_t)delta << 32) | (uint64_t)row;
+                    if (key < tau[gq]) {
+                        // warp-aggregated: one slot reservation and one
+                        // minimum per warp and query
+                        const unsigned am = __activemask();
+                        const int leader = __ffs(am) - 1;
+                        const int rank = __popc(am & ((1u << lane) - 1u));
+                        int pos0 = 0;
+                        if (lane == leader) pos0 = atomicAdd(&cnt[gq], __popc(am));
+                        pos0 = __shfl_sync(am, pos0, leader);
+                        cand[gq * CAND_CAP + pos0 + rank] = key;
+                        // each row is appended at most once: count it for the union bound
+                        const uint32_t h = delta >> 1;
+                        atomicAdd(&a.hist[gq * a.hist_bins + h], 1u);
+                        const uint32_t wmin = __reduce_min_sync(am, h);
+                        if (lane == leader && wmin < lmin[gq]) {
+                            atomicMin(&lmin[gq], wmin);
+                            atomicMin(&a.minhalf[gq], wmin);
+                        }
+                    }
+                }
+            }
         }
     }
 
@@ -575,16 +605,33 @@ int choose_stages(int W, int qb) {
     return 0;
 }
 
-template <int QB, int TPR>
-cudaError_t launch_scan(const CUtensorMap& tmap, const ScanArgs& a, int nslices, size_t smem,
-                        cudaStream_t stream) {
-    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<QB, TPR>,
+template <int QB, int TPR, int WW, bool EXACT>
+cudaError_t launch_scan_w(const CUtensorMap& tmap, const ScanArgs& a, int nslices, size_t smem,
+                          cudaStream_t stream) {
+    cudaError_t e = cudaFuncSetAttribute(scan_popc_kernel<QB, TPR, WW, EXACT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          SMEM_BUDGET + 2048);
     if (e != cudaSuccess) return e;
     TimedLaunch timer("scan_popc", stream);
-    scan_popc_kernel<QB, TPR><<<nslices, SCAN_ROWS * TPR, smem, stream>>>(tmap, a);
+    scan_popc_kernel<QB, TPR, WW, EXACT><<<nslices, SCAN_ROWS * TPR, smem, stream>>>(tmap, a);
     return cudaGetLastError();
+}
+
+// Rows are held in registers, WW >= W words per plane: the common widths
+// (d = 384, 768, 1024) exactly, the others padded to the next of 4, 8, 12, 16.
+template <int QB, int TPR>
+cudaError_t launch_scan(const CUtensorMap& tmap, const ScanArgs& a, int nslices, size_t smem,
+                        cudaStream_t stream) {
+    switch (a.W) {
+        case 6: return launch_scan_w<QB, TPR, 6, true>(tmap, a, nslices, smem, stream);
+        case 12: return launch_scan_w<QB, TPR, 12, true>(tmap, a, nslices, smem, stream);
+        case 16: return launch_scan_w<QB, TPR, 16, true>(tmap, a, nslices, smem, stream);
+        default: break;
+    }
+    if (a.W <= 4) return launch_scan_w<QB, TPR, 4, false>(tmap, a, nslices, smem, stream);
+    if (a.W <= 8) return launch_scan_w<QB, TPR, 8, false>(tmap, a, nslices, smem, stream);
+    if (a.W <= 12) return launch_scan_w<QB, TPR, 12, false>(tmap, a, nslices, smem, stream);
+    return launch_scan_w<QB, TPR, 16, false>(tmap, a, nslices, smem, stream);
 }
 
 }  // namespace
