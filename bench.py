@@ -77,7 +77,16 @@ KERNEL_SOURCES = {
     "scan_popc": ["paper_2506_00528_gb300/csrc/scan_popc.cu",
                   "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
 }
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
+    ("scan_mma", 10_000_000, 768, 1024, 100): {
+        "bytes": 7_721_389_312 + 4_181_248,
+        "sources_sha256": "3b4c3e7031ef3a5d0cdefb01c318bfc9df6e37251c8519a01d886b8d7494a488"},
+    # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
+    ("scan_popc", 10_000_000, 768, 1, 100): {
+        "bytes": 1_920_046_592 + 3_111_936,
+        "sources_sha256": "f5e8969448f80220e1da03d6bf7ccb4d013d6c216231adccaeb2f949de5b189e"},
+}
 
 
 def kernel_sources_sha(kernel: str) -> str:
