@@ -597,24 +597,31 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 // columns of this group inside the slice (the last tile is ragged)
                 const int64_t left = row_end - (tile_row + c * 32);
                 const int lim = !valid_q ? 0 : (left >= 32 ? 32 : (left > 0 ? (int)left : 0));
-                int nsub = 0;
+                uint32_t my8 = 0;  // this lane's 4-column sub-groups with a candidate
 #pragma unroll
-                for (int i = 0; i < 8; ++i) nsub += (sm[i] > thr && 4 * i < lim) ? 1 : 0;
+                for (int i = 0; i < 8; ++i) my8 |= (sm[i] > thr && 4 * i < lim) ? 1u << i : 0u;
+                // sub-groups in which any lane has a candidate (one reduction
+                // instead of a vote per sub-group; still valid after a flush,
+                // which only raises the threshold)
+                const uint32_t all8 = __reduce_or_sync(0xffffffffu, my8);
                 // flush first if this group could overflow a lane's staging
-                if (__any_sync(0xffffffffu, sc + 4 * nsub > STAGE_SLOTS)) {
+                if (__any_sync(0xffffffffu, sc + 4 * __popc(my8) > STAGE_SLOTS)) {
                     flush();
                     thr = fmaxf(dtau, dglob);
                 }
                 const uint32_t gbase = (uint32_t)(tile_row + c * 32 - row0);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    if (!__any_sync(0xffffffffu, sm[i] > thr && 4 * i < lim)) continue;
+                    if (!((all8 >> i) & 1u)) continue;
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = 4 * i + jj;
                         const float dv = __uint_as_float(v[j]);
                         if (dv > thr && j < lim) {
-                            const uint32_t half_delta = (uint32_t)(a.x - __float2int_rn(dv));
+                            // D is an integer below 2^22 in magnitude: adding
+                            // 1.5 * 2^23 leaves it in the low mantissa bits
+                            const int di = __float_as_int(dv + 12582912.0f) - 0x4B400000;
+                            const uint32_t half_delta = (uint32_t)(a.x - di);
                             staging[sc * MMA_M + m] = (half_delta << LOCAL_BITS) | (gbase + (uint32_t)j);
                             ++sc;
                         }
