@@ -80,8 +80,8 @@ KERNEL_SOURCES = {
 MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 7_721_389_312 + 4_181_248,
-        "sources_sha256": "3b4c3e7031ef3a5d0cdefb01c318bfc9df6e37251c8519a01d886b8d7494a488"},
+        "bytes": 7_693_122_304 + 4_308_480,
+        "sources_sha256": "325ae8f098e18935a0856eb8bdc9f6c7f895e7f019167340786c185ebce6cc33"},
     # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
     ("scan_popc", 10_000_000, 768, 1, 100): {
         "bytes": 1_920_046_592 + 3_111_936,
