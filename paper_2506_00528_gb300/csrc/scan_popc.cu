@@ -11,12 +11,16 @@
 // the four-term bitplane scalar product of Sec. 5.1.2.
 //
 // Kernel layout (one CTA per SM, persistent over a contiguous slice of the
-// database; 256 threads, one database row per thread per tile):
+// database; 256 threads for a one-query pass, otherwise 512, two per row
+// each taking half of the pass's queries):
 //   * database tiles of 256 rows are staged into shared memory by TMA
 //     (cp.async.bulk.tensor.2d) through a ring of mbarrier-tracked stages.
 //     The box is wider than a row (2(W+p) words, p chosen so the row
 //     pitch in 16-byte units is odd); the extra words are filled with 0 by
 //     the TMA unit and make the per-thread row reads bank-conflict free;
+//   * each thread copies its row into registers, the stage is released at
+//     once (its next copy is issued while the rows are scored), and the row
+//     is scored from registers;
 //   * the pass's queries (up to 16) sit in shared memory as (m, sigma)
 //     word pairs and are read by broadcast;
 //   * a row whose key (Delta << 32 | row) beats the query's threshold tau
@@ -33,8 +37,9 @@
 //   * a merge is done by a team of warps per query (all warps of the CTA
 //     take part whatever the pass size): bitonic sort, merge path, and the
 //     histogram scan for the bound.
-// A second kernel merges, per query, the slice lists' keys that do not
-// exceed the final global threshold into the k best.
+// A second kernel merges, per query, the slice lists into the k best: the
+// keys at or below the union bound of the complete histogram are gathered
+// and sorted directly when there are few of them.
 #include "evp_internal.cuh"
 
 #include <algorithm>
