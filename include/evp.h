@@ -174,8 +174,9 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
  *                  one byte per element (in the workspace when S is given
  *                  packed).  A 128-query tile serves all 128 queries for
  *                  k <= 128 and fewer (64, 32, 16) for larger k.
- *   EVP_PATH_AUTO  MMA when nq > 16, POPC otherwise.  This is what
- *                  ternary_knn uses.
+ *   EVP_PATH_AUTO  MMA when nq > 16, POPC otherwise (against a resident
+ *                  database holding its e4m3 copy: MMA when nq > 8).  This
+ *                  is what ternary_knn and evp_db_knn/evp_db_search use.
  * The MMA path assumes every code has exactly x non-zeros (as evp_encode
  * produces): it computes Delta as 2x - 2*b2sp.  The POPC path computes
  * ||q - s||^2 directly. */

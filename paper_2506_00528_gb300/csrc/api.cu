@@ -127,7 +127,8 @@ int32_t evp_encode(const float* U, int64_t n, int32_t d, int32_t x, uint64_t* T,
 namespace {
 
 int resolve_path(int64_t nq, int32_t k, int32_t path) {
-    if (path == EVP_PATH_AUTO) return (nq > 16 && k <= MMA_K_MAX) ? EVP_PATH_MMA : EVP_PATH_POPC;
+    if (path == EVP_PATH_AUTO)
+        return (nq >= auto_mma_min_nq(false) && k <= MMA_K_MAX) ? EVP_PATH_MMA : EVP_PATH_POPC;
     return path;
 }
 
@@ -137,12 +138,12 @@ size_t evp::knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool co
     if (nq <= 0) return 0;
     size_t best = 0;
     // popcount path: its workspace does not depend on nq
-    if (path == EVP_PATH_POPC || (path == EVP_PATH_AUTO && resolve_path(1, k, path) == EVP_PATH_POPC))
+    if (path == EVP_PATH_POPC || path == EVP_PATH_AUTO)
         best = plan_popc_scan(std::min<int64_t>(nq, 16), ns, d, k).ws_bytes;
     // tensor path, taken by AUTO from nq0 queries up: the slice count depends
     // on the number of query tiles, so the lists can need more room at fewer
     // queries; the largest call in each tile count is the last one
-    const int64_t nq0 = path == EVP_PATH_MMA ? 1 : 17;
+    const int64_t nq0 = path == EVP_PATH_MMA ? 1 : auto_mma_min_nq(!convert_db);
     if ((path == EVP_PATH_MMA || path == EVP_PATH_AUTO) && k <= MMA_K_MAX && nq >= nq0) {
         const int64_t qa = mma_active_queries(k);
         for (int64_t t = (nq0 + qa - 1) / qa; t <= (nq + qa - 1) / qa; ++t)

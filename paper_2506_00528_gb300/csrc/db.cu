@@ -20,8 +20,10 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-int resolve_db_path(int64_t nq, int32_t k, int32_t path) {
-    if (path == EVP_PATH_AUTO) return (nq > 16 && k <= MMA_K_MAX) ? EVP_PATH_MMA : EVP_PATH_POPC;
+int resolve_db_path(const evp_db* db, int64_t nq, int32_t k, int32_t path) {
+    if (path == EVP_PATH_AUTO)
+        return (nq >= auto_mma_min_nq(db->S8 != nullptr) && k <= MMA_K_MAX) ? EVP_PATH_MMA
+                                                                              : EVP_PATH_POPC;
     return path;
 }
 
@@ -113,7 +115,7 @@ int32_t evp_db_knn(evp_db_t db, const uint64_t* Q, int64_t nq, int32_t k, int64_
     if (nq < 0 || k < 1 || (int64_t)k > db->ns || path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
         return EVP_ERR_INVALID;
     if (k > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
-    const int rp = resolve_db_path(nq, k, path);
+    const int rp = resolve_db_path(db, nq, k, path);
     if (rp == EVP_PATH_MMA && k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
     if (nq == 0) return EVP_OK;
     if (!Q || !ids || !dist || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)

@@ -194,19 +194,27 @@ struct MmaPlan {
     int qtiles;             // query tiles (of qa queries)
     int nslices;            // database slices per query tile
     int cg;                 // CTAs per tensor-core instruction: 1, or 2 (a CTA pair)
+    bool spread;            // <= 128 queries spread over every epilogue warp's lanes
     int workers;            // resident CTAs (cg = 1) or CTA pairs (cg = 2)
     int64_t rows_per_slice;
     size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, hist_bytes, ws_bytes;
 };
 constexpr int MMA_K_MAX = 1024;  // largest k of the tensor-core path
+// Smallest query count for which the automatic choice takes the tensor-core
+// scan: from 9 queries when the database's e4m3 copy is resident (the scan
+// then reads 1 byte per element at HBM speed, faster than a 16-query
+// popcount pass), from 17 when the copy must be built first.
+inline int64_t auto_mma_min_nq(bool resident_copy) { return resident_copy ? 9 : 17; }
 int mma_kp(int d);
 // Workspace bytes that serve every kNN call with at most nq queries (and
 // the same other arguments) on `path` (AUTO resolved per call).
 size_t knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert_db);
 int mma_active_queries(int k);
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db);
+// spread_cg > 0: query rows placed as the tensor-core scan's small-batch
+// spread over spread_cg CTAs expects (queries only).
 cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
-                              cudaStream_t stream);
+                              cudaStream_t stream, int spread_cg = 0);
 // S8: resident e4m3 copy of the database ([ns][kp]) or nullptr, in which case
 // S is converted into the workspace first.
 int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint64_t* S,

@@ -102,6 +102,8 @@ struct MmaArgs {
     int64_t rows_per_slice;
     int qtiles, nslices;   // work items = qtiles * nslices
     int qa;                // active queries per 128-row tile (k <= HEAP_SLOTS / qa)
+    int spread;            // a batch of <= 128 queries spread over every TMEM lane quadrant
+                           // of both CTAs (see query_of_lane)
     uint64_t* lists;       // [nq][nslices][2][k], buffer 0 used
     int32_t* meta;         // [nq][nslices][2]
     uint64_t* tau_global;  // [nq] (unused by the tensor path)
@@ -278,6 +280,19 @@ __device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
           "+r"(v[31])
         :
         : "memory");
+}
+
+// Small batches (at most 128 queries, qa = 128) are spread over the lanes of
+// all epilogue warps (and both CTAs of a pair) instead of filling the first
+// lanes of one tile: query i sits in CTA i % CG, lane m = 32 (j % 4) + j / 4
+// with j = i / CG.  The inverse maps a lane back to its query.
+__host__ __device__ __forceinline__ int64_t lane_of_query(int64_t i, int cg) {
+    const int64_t j = i / cg;
+    return (i % cg) * 128 + (j % 4) * 32 + j / 4;
+}
+__device__ __forceinline__ int64_t query_of_lane(int m, int rank, int cg) {
+    const int j = (m & 31) * 4 + (m >> 5);
+    return (int64_t)j * cg + rank;
 }
 
 // Max-heap of u32 keys, element i of thread m at h[i * qa + m] (qa = active
@@ -517,8 +532,8 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int slice = w.slice, ntiles = w.ntiles;
         const int64_t row0 = w.row0, row_end = w.row_end;
         const int qa = a.qa;
-        const int64_t qrow = (int64_t)w.qt * qa + m;
-        const bool valid_q = m < qa && qrow < a.nq;
+        const int64_t qrow = a.spread ? query_of_lane(m, (int)rank, CG) : (int64_t)w.qt * qa + m;
+        const bool valid_q = (a.spread || m < qa) && qrow < a.nq;
         uint32_t* hist = a.hist + (valid_q ? qrow : 0) * (int64_t)a.hist_bins;
         if (warp == 2 && lane == 0) *reinterpret_cast<volatile int*>(cur_item) = item;
         int hs = 0;
@@ -714,8 +729,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll 1
             for (int j = 0; j < MMA_M / 32; ++j) {
                 const int mm = j * 32 + lane;
-                const int64_t qrow = (int64_t)qt * a.qa + mm;
-                if (mm >= a.qa || qrow >= a.nq) continue;
+                const int64_t qrow =
+                    a.spread ? query_of_lane(mm, (int)rank, CG) : (int64_t)qt * a.qa + mm;
+                if ((!a.spread && mm >= a.qa) || qrow >= a.nq) continue;
                 const uint32_t lo = __ldcg(&a.minhalf[qrow]);
                 if (lo == 0xFFFFFFFFu) continue;
                 const uint32_t* hist = a.hist + qrow * (int64_t)a.hist_bins;
@@ -767,8 +783,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 }
 
 // Packed codes -> e4m3 rows [n][Kp] (Kp a multiple of 128; columns >= d are 0).
+// spread_cg > 0: row i goes to lane_of_query(i, spread_cg) instead of i.
 __global__ void unpack_fp8_kernel(const uint64_t* __restrict__ T, int64_t n, int W, int Kp,
-                                  uint8_t* __restrict__ out) {
+                                  int spread_cg, uint8_t* __restrict__ out) {
     const int groups = Kp / 16;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t row = idx / groups;
@@ -792,7 +809,8 @@ __global__ void unpack_fp8_kernel(const uint64_t* __restrict__ T, int64_t n, int
         }
         o[i] = word;
     }
-    reinterpret_cast<uint4*>(out + row * (int64_t)Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
+    const int64_t orow = spread_cg > 0 ? lane_of_query(row, spread_cg) : row;
+    reinterpret_cast<uint4*>(out + orow * (int64_t)Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
 }
 
 __global__ void init_tau_n_kernel(uint64_t* tau, int n, uint32_t* hist, int64_t hist_words,
@@ -865,6 +883,10 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
     const int pairs = mma_pair_workers();
     p.cg = pairs > 0 ? 2 : 1;
     p.workers = pairs > 0 ? pairs : num_sms();
+    // a single tile's worth of queries is spread over every epilogue warp
+    // (and both CTAs of a pair), so that no warp carries all the candidates
+    p.spread = p.qa == MMA_M && nq <= MMA_M;
+    if (p.spread) p.qtiles = p.cg;
     const int units = (p.qtiles + p.cg - 1) / p.cg;
     const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
     const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
@@ -895,12 +917,13 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
 }
 
 cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
-                              cudaStream_t stream) {
+                              cudaStream_t stream, int spread_cg) {
     if (n <= 0) return cudaSuccess;
     const int W = (d + 63) / 64, Kp = mma_kp(d);
     const int64_t threads = n * (Kp / 16);
     TimedLaunch timer("unpack_fp8", stream);
-    unpack_fp8_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(T, n, W, Kp, out);
+    unpack_fp8_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(T, n, W, Kp,
+                                                                               spread_cg, out);
     return cudaGetLastError();
 }
 
@@ -923,7 +946,9 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
         reinterpret_cast<uint8_t*>(hist) + align256((size_t)nq * (2 * d + 1) * 4));
     if ((reinterpret_cast<uintptr_t>(B8) & 255) != 0) return EVP_ERR_INVALID;
 
-    if (launch_unpack_fp8(Q, nq, d, A8, stream) != cudaSuccess) return EVP_ERR_CUDA;
+    if (p.spread && cudaMemsetAsync(A8, 0, p.a_bytes, stream) != cudaSuccess) return EVP_ERR_CUDA;
+    if (launch_unpack_fp8(Q, nq, d, A8, stream, p.spread ? p.cg : 0) != cudaSuccess)
+        return EVP_ERR_CUDA;
     if (!S8 && launch_unpack_fp8(S, ns, d, B8, stream) != cudaSuccess) return EVP_ERR_CUDA;
     {
         TimedLaunch timer("scan_init", stream);
@@ -936,7 +961,7 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     EncodeTiledFn enc = encode_tiled_fn();
     if (!enc) return EVP_ERR_CUDA;
     CUtensorMap tmA, tmB;
-    cuuint64_t gdimA[2] = {(cuuint64_t)p.kp, (cuuint64_t)nq};
+    cuuint64_t gdimA[2] = {(cuuint64_t)p.kp, (cuuint64_t)(p.spread ? p.qtiles * MMA_M : nq)};
     cuuint64_t gdimB[2] = {(cuuint64_t)p.kp, (cuuint64_t)ns};
     cuuint64_t gstride[1] = {(cuuint64_t)p.kp};
     cuuint32_t boxA[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)MMA_M};
@@ -960,6 +985,7 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.rows_per_slice = p.rows_per_slice;
     args.qtiles = p.qtiles;
     args.qa = p.qa;
+    args.spread = p.spread ? 1 : 0;
     args.nslices = p.nslices;
     args.lists = lists;
     args.meta = meta;
