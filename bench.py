@@ -80,12 +80,12 @@ KERNEL_SOURCES = {
 MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 7_693_122_304 + 4_308_480,
-        "sources_sha256": "325ae8f098e18935a0856eb8bdc9f6c7f895e7f019167340786c185ebce6cc33"},
+        "bytes": 7_694_802_176 + 4_100_096,
+        "sources_sha256": "e9175fa019fa880ed8b8195809b7a395f0569b30db5a61151ba740108a774aec"},
     # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
     ("scan_popc", 10_000_000, 768, 1, 100): {
-        "bytes": 1_920_046_592 + 3_111_936,
-        "sources_sha256": "f5e8969448f80220e1da03d6bf7ccb4d013d6c216231adccaeb2f949de5b189e"},
+        "bytes": 1_920_047_616 + 3_326_976,
+        "sources_sha256": "08f0eb4023a2f101009c110d6158fdf9d2da78a63c1428e6faf98ed19e5457be"},
 }
 
 
