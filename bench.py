@@ -50,6 +50,10 @@ def parse():
                     help="skip the batched-form and served-form measurements")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--serve-rate", type=float, default=150.0, help="requests/s (Poisson)")
+    ap.add_argument("--recall-sweep", action="store_true",
+                    help="instead of the benchmark: recall of the ternary scan against exact "
+                         "float32 cosine kNN for several x (1M x 768 mixture by default)")
+    ap.add_argument("--sweep-queries", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -341,10 +345,76 @@ def main_reference(a):
     }))
 
 
+def exact_topk(Qf, U, k, chunk=1 << 18):
+    """Exact float32 top-k by scalar product (cosine on normalised rows)."""
+    import torch
+    torch.backends.cuda.matmul.allow_tf32 = False
+    nq = Qf.shape[0]
+    best_s = torch.full((nq, k), -float("inf"), device=Qf.device)
+    best_i = torch.zeros((nq, k), dtype=torch.int64, device=Qf.device)
+    for c0 in range(0, U.shape[0], chunk):
+        sc = Qf @ U[c0:c0 + chunk].T
+        v, i = torch.topk(sc, min(k, sc.shape[1]), dim=1)
+        cat_s = torch.cat([best_s, v], 1)
+        cat_i = torch.cat([best_i, i + c0], 1)
+        best_s, j = torch.topk(cat_s, k, dim=1)
+        best_i = torch.gather(cat_i, 1, j)
+    return best_i
+
+
+def main_recall_sweep(a):
+    """Recall of the ternary proxy against exact float32 cosine kNN, per x:
+    ternary top-K vs exact top-K (recall@K), and the best k after reranking
+    a 10k shortlist vs the exact top-k.  Reported, not pinned."""
+    import torch
+    from paper_2506_00528_gb300 import build as _build
+    from paper_2506_00528_gb300 import evp, synth
+    dev = torch.device("cuda", 0)
+    _build.build()
+    evp.load()
+    n = a.n if a.n != 10_000_000 else 1_000_000
+    d, nqs = a.d, a.sweep_queries
+    U = synth.mixture_torch(n, d, n_centres=a.centres, anisotropic=True,
+                            stream=synth.STREAM_DB, device=dev)
+    Q = synth.mixture_torch(nqs, d, n_centres=a.centres, anisotropic=True,
+                            stream=synth.STREAM_QUERIES, device=dev)
+    K, k = 100, 10
+    truth_K = exact_topk(Q, U, K).cpu().numpy()
+    truth_k = truth_K[:, :k]
+    out = {"kind": "recall_sweep", "n": n, "d": d, "queries": nqs, "path": "popcount",
+           "data": "synthetic Gaussian mixture, 1024 centres, anisotropic, l2-normalised",
+           "recall": {}}
+    for x in sorted({64, 256, 384, evp.default_x(d)}):
+        T = evp.encode(U, x)
+        Tq = evp.encode(Q, x)
+        db = evp.Database(T, U, d, x, tensor_copy=False)
+        ids_K = torch.empty((nqs, K), dtype=torch.int64, device=dev)
+        for q0 in range(0, nqs, 1024):
+            ids, _ = db.knn(Tq[q0:q0 + 1024], K, path=1)
+            ids_K[q0:q0 + 1024] = ids
+        got_K = ids_K.cpu().numpy()
+        rr_ids = torch.empty((nqs, k), dtype=torch.int64, device=dev)
+        for q0 in range(0, nqs, 1024):
+            ids, _ = db.search(Q[q0:q0 + 1024].contiguous(), 10 * k, k)
+            rr_ids[q0:q0 + 1024] = ids
+        got_rr = rr_ids.cpu().numpy()
+        rec = lambda g, t, m: float(np.mean([len(set(a_[:m]) & set(b_[:m])) / m
+                                             for a_, b_ in zip(g, t)]))
+        out["recall"][str(x)] = {"recall_at_100": rec(got_K, truth_K, K),
+                                 "recall_at_10": rec(got_K, truth_K, k),
+                                 "rerank_10_of_100": rec(got_rr, truth_k, k)}
+        db.close()
+        del T, db
+        torch.cuda.empty_cache()
+    print(json.dumps(out))
+
+
 def main():
     a = parse()
     if a.impl == "reference":
         return main_reference(a)
+    if a.recall_sweep:
+        return main_recall_sweep(a)
 
     import torch
     import torch.distributed as dist
