@@ -6,6 +6,9 @@
 * 10,000,000 x 768, x = 512, 1,024 queries, shortlist 100 then rerank to
   10 -- the benchmark's launch configuration -- checked on sampled queries
   through properties the oracle computes row by row.
+* 10,000,000 x 1024, x = 256, 4,096 queries (the large dense contraction):
+  the resident database's tensor-core scan, shortlist 100, rerank to 10,
+  checked the same way.
 """
 import numpy as np
 import pytest
@@ -80,3 +83,39 @@ def test_bench_workload_10m_sampled(evp_lib, dev):
         gi = rid.cpu().numpy()[q:q + 1]
         g_local = np.array([[int(np.where(sl_h[q] == i)[0][0]) for i in gi[0]]])
         check_rerank(g_local, rsc.cpu().numpy()[q:q + 1], Q_h[q:q + 1], S_rows, local, k)
+
+
+def test_dense_contraction_10m_1024_sampled(evp_lib, dev):
+    n, d, x, nq, n_sl, k = 10_000_000, 1024, 256, 4096, 100, 10
+    U = synth.mixture_torch(n, d, n_centres=1024, anisotropic=True, stream=synth.STREAM_DB,
+                            device=dev)
+    Q = synth.mixture_torch(nq, d, n_centres=1024, anisotropic=True,
+                            stream=synth.STREAM_QUERIES, device=dev)
+    st = evp_lib.new_status(dev)
+    Ts = evp_lib.encode(U, x, status=st)
+    Tq = evp_lib.encode(Q, x, status=st)
+    db = evp_lib.Database(Ts, U, d, x)
+    sl, sd = db.knn(Tq, n_sl, status=st)
+    rid, rsc = db.search(Q, n_sl, k, status=st)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    rng = np.random.default_rng(321)
+    sample_idx = np.sort(rng.choice(n, 30_000, replace=False))
+    U_sample = U[torch.from_numpy(sample_idx).to(dev)].cpu().numpy()
+    V_sample = par_encode(U_sample, x)
+    np.testing.assert_array_equal(Ts[torch.from_numpy(sample_idx).to(dev)].cpu().numpy()
+                                  .view(np.uint64), oracle.pack(V_sample))
+    Q_h = Q.cpu().numpy()
+    sel = (0, 129, 2048, 4095)   # several query tiles and both CTAs of a pair
+    Vq = oracle.encode(Q_h[list(sel)], x)
+    sl_h, sd_h = sl.cpu().numpy(), sd.cpu().numpy()
+    rid_h, rsc_h = rid.cpu().numpy(), rsc.cpu().numpy()
+    for i, q in enumerate(sel):
+        rows = U[torch.from_numpy(sl_h[q]).to(dev)].cpu().numpy()
+        check_knn_sampled(Vq[i], sl_h[q], sd_h[q], oracle.encode(rows, x), V_sample, sample_idx)
+        # the search's rerank reorders this same shortlist
+        gi = rid_h[q]
+        g_local = np.array([[int(np.where(sl_h[q] == j)[0][0]) for j in gi]])
+        local = np.arange(n_sl, dtype=np.int64)[None, :]
+        check_rerank(g_local, rsc_h[q:q + 1], Q_h[q:q + 1], rows, local, k)
+    db.close()
