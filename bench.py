@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--centres", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
-    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 popcount, 2 tensor core")
+    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 popcount, 2 tensor core, 3 packed tensor core")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-form and served-form measurements")
     ap.add_argument("--serve-seconds", type=float, default=4.0)
@@ -80,6 +80,8 @@ KERNEL_SOURCES = {
                  "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
     "scan_popc": ["paper_2506_00528_gb300/csrc/scan_popc.cu",
                   "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
+    "scan_mma_packed": ["paper_2506_00528_gb300/csrc/scan_mma_packed.cu",
+                        "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
 }
 MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
@@ -262,7 +264,8 @@ def measure_batched(evp, synth, dev, seed_batches=64):
     return {"batches": seed_batches, "queries": total_q,
             "graph_qps": total_q / (graph_ms / 1e3), "graph_ms": graph_ms,
             "plain_qps": total_q / (plain_ms / 1e3), "plain_ms": plain_ms,
-            "paths": {"popc": paths.count(1), "mma": paths.count(2)},
+            "paths": {"popc": paths.count(1), "mma": paths.count(2),
+                      "mma_packed": paths.count(3)},
             "identical_results": bool(same),
             "workload": "3 DBs (1Mx384 x128, 4Mx768 x256, 2Mx1024 x384), 64 kNN batches "
                         "logU[1,8192] queries, k in {10,100}"}
@@ -457,7 +460,7 @@ def main():
     Qall = synth.mixture_torch(pool * B, d, n_centres=a.centres, anisotropic=True,
                                stream=synth.STREAM_QUERIES + 10 * rank, device=dev)
     Qb = [Qall[i * B:(i + 1) * B] for i in range(pool)]
-    db = evp.Database(S, U, d, x, tensor_copy=(a.path != 1))
+    db = evp.Database(S, U, d, x, tensor_copy=(a.path not in (1, 3)))
     Tq = torch.empty((B, 2 * W), dtype=torch.int64, device=dev)
     sl = torch.empty((B, n_sl), dtype=torch.int64, device=dev)
     sd = torch.empty((B, n_sl), dtype=torch.int32, device=dev)
@@ -506,7 +509,7 @@ def main():
     ms = e0.elapsed_time(e1)
     per_kernel = {name: evp.timing_read(name) for name in
                   ("encode", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
-                               "final_merge", "rerank")}
+                   "scan_mma_packed", "final_merge", "rerank")}
     evp.check_status(st, "timed steps")
     # replicas: every rank searched its own B queries per step; the job's
     # throughput is all ranks' queries over the slowest rank's time
@@ -549,7 +552,32 @@ def main():
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     n_mma, mma_ms = per_kernel["scan_mma"]
     n_scan, scan_ms = per_kernel["scan_popc"]
-    if mma_ms >= scan_ms:
+    n_pk, pk_ms = per_kernel["scan_mma_packed"]
+    if pk_ms > max(mma_ms, scan_ms):
+        # packed tensor-core scan: one launch per <= 64 queries reads the
+        # packed codes (16 W bytes per row) once; 2 d flops per (query, row)
+        avg = pk_ms / max(1, n_pk)
+        passes_per_step = (B + 63) // 64
+        bytes_per_launch = float(n) * 16 * W
+        flops = 2.0 * d * n * (B / passes_per_step)
+        fp8_peak = 2.0 * bf16_peak
+        gbs = bytes_per_launch / (avg / 1e3) / 1e9
+        tflops = flops / (avg / 1e3) / 1e12
+        tensor_frac, hbm_frac = tflops / fp8_peak, gbs / hbm_peak
+        if tensor_frac >= hbm_frac:
+            bound = {"bound": "tensor", "achieved": tflops, "peak": fp8_peak, "unit": "TFLOP/s",
+                     "frac": tensor_frac}
+        else:
+            bound = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": hbm_frac}
+        roofline = {
+            "kernel": "scan_mma_packed", **bound,
+            "traffic": measured_traffic("scan_mma_packed", n, d, B, a.shortlist),
+            "tensor_frac": tensor_frac, "hbm_frac": hbm_frac, "packed_gbs": gbs,
+            "peak_source": f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s; HBM {hbm_peak} GB/s ({peak_src})",
+            "launches": n_pk, "avg_ms": avg,
+        }
+    elif mma_ms >= scan_ms:
         # tensor-core scan: algorithmic flops = 2 d per (query, row) pair; it
         # reads the database's e4m3 copy (Kp bytes per row) once per launch,
         # which binds instead for small batches

@@ -166,23 +166,40 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
                            int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist,
                            int32_t* dev_status, void* stream);
 
-/* Scan paths.  Both return identical results.
+/* Scan paths.  All return identical results.
  *   EVP_PATH_POPC  bitplane popcount scan on the integer pipe: reads the
- *                  packed codes once per 16 queries; best for small batches.
+ *                  packed codes once per 16 queries; best for up to three
+ *                  queries.
  *   EVP_PATH_MMA   tensor-core scan (tcgen05, e4m3 operands holding -1/0/+1,
- *                  float32 accumulation, exact): the codes are expanded to
- *                  one byte per element (in the workspace when S is given
- *                  packed).  A 128-query tile serves all 128 queries for
- *                  k <= 128 and fewer (64, 32, 16) for larger k.
- *   EVP_PATH_AUTO  MMA when nq > 16, POPC otherwise (against a resident
- *                  database holding its e4m3 copy: MMA when nq > 8).  This
- *                  is what ternary_knn and evp_db_knn/evp_db_search use.
- * The MMA path assumes every code has exactly x non-zeros (as evp_encode
- * produces): it computes Delta as 2x - 2*b2sp.  The POPC path computes
- * ||q - s||^2 directly. */
+ *                  float32 accumulation, exact) with the queries as the
+ *                  128-row side: the codes are expanded to one byte per
+ *                  element (in the workspace when S is given packed, or
+ *                  once for a database created with EVP_DB_TENSOR_COPY).
+ *                  A 128-query tile serves all 128 queries for k <= 128 and
+ *                  fewer (64, 32, 16) for larger k; best for large batches.
+ *   EVP_PATH_MMA_PACKED  tensor-core scan with the database as the 128-row
+ *                  side: reads the packed codes once per 64 queries and
+ *                  unpacks each tile on chip into tensor memory; needs
+ *                  d <= 768 with ceil(d/64) even (else EVP_ERR_UNSUPPORTED)
+ *                  and at most 2^20 * 1024 rows; best for medium batches.
+ *   EVP_PATH_AUTO  POPC for nq <= EVP_AUTO_POPC_MAX_NQ; MMA_PACKED (where
+ *                  supported) up to EVP_AUTO_PACKED_MAX_NQ queries against a
+ *                  resident database holding its e4m3 copy, and up to
+ *                  EVP_AUTO_PACKED_MAX_NQ_NO_COPY otherwise (MMA would first
+ *                  expand the database); MMA beyond.  Where the packed path
+ *                  does not apply: MMA when nq > 16 (> 8 with a resident
+ *                  copy), POPC otherwise.  This is what ternary_knn and
+ *                  evp_db_knn/evp_db_search use.
+ * The tensor-core paths assume every code has exactly x non-zeros (as
+ * evp_encode produces): they compute Delta as 2x - 2*b2sp.  The POPC path
+ * computes ||q - s||^2 directly. */
 #define EVP_PATH_AUTO 0
 #define EVP_PATH_POPC 1
 #define EVP_PATH_MMA  2
+#define EVP_PATH_MMA_PACKED 3
+#define EVP_AUTO_POPC_MAX_NQ 3
+#define EVP_AUTO_PACKED_MAX_NQ 48
+#define EVP_AUTO_PACKED_MAX_NQ_NO_COPY 128
 #define EVP_MMA_MAX_K 1024
 
 size_t ternary_knn_path_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k,
@@ -314,11 +331,12 @@ int32_t evp_db_search_host(evp_db_t db, const float* Q_host, int64_t nq, int32_t
  * outputs ids and dist, as evp_db_knn).  All pointers are device pointers
  * owned by the caller and must stay valid while the plan exists.
  *
- * evp_autotune times the popcount and tensor-core scans on a database for
- * a query count (rounded up to a power of two) and k, using the database's
- * own rows as trial queries, and caches the faster path per (database,
- * query-count bucket, k); *path_out receives it, and *popc_ms / *mma_ms
- * (optional) the timings, which force a fresh measurement when requested.
+ * evp_autotune times the popcount and both tensor-core scans (where they
+ * apply) on a database for a query count (rounded up to a power of two)
+ * and k, using the database's own rows as trial queries, and caches the
+ * fastest path per (database, query-count bucket, k); *path_out receives
+ * it, *popc_ms (optional) the popcount time and *mma_ms (optional) the
+ * faster tensor-core time; asking for a timing forces a fresh measurement.
  * It allocates temporary device memory.
  *
  * evp_batch_plan_create checks every descriptor, picks each batch's path

@@ -124,12 +124,19 @@ int32_t evp_encode(const float* U, int64_t n, int32_t d, int32_t x, uint64_t* T,
 
 }  // extern "C"
 
+int evp::auto_path(int64_t nq, int64_t ns, int d, int k, bool resident_copy) {
+    if (k <= MMA_K_MAX && mma_packed_supported(ns, d, k)) {
+        if (nq <= EVP_AUTO_POPC_MAX_NQ) return EVP_PATH_POPC;
+        return nq <= auto_packed_max_nq(resident_copy) ? EVP_PATH_MMA_PACKED : EVP_PATH_MMA;
+    }
+    return (nq >= auto_mma_min_nq(resident_copy) && k <= MMA_K_MAX) ? EVP_PATH_MMA
+                                                                     : EVP_PATH_POPC;
+}
+
 namespace {
 
-int resolve_path(int64_t nq, int32_t k, int32_t path) {
-    if (path == EVP_PATH_AUTO)
-        return (nq >= auto_mma_min_nq(false) && k <= MMA_K_MAX) ? EVP_PATH_MMA : EVP_PATH_POPC;
-    return path;
+int resolve_path(int64_t nq, int64_t ns, int32_t d, int32_t k, int32_t path) {
+    return path == EVP_PATH_AUTO ? auto_path(nq, ns, d, k, false) : path;
 }
 
 }  // namespace
@@ -137,13 +144,20 @@ int resolve_path(int64_t nq, int32_t k, int32_t path) {
 size_t evp::knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert_db) {
     if (nq <= 0) return 0;
     size_t best = 0;
-    // popcount path: its workspace does not depend on nq
+    // popcount path (AUTO takes it for one query): its workspace does not depend on nq
     if (path == EVP_PATH_POPC || path == EVP_PATH_AUTO)
         best = plan_popc_scan(std::min<int64_t>(nq, 16), ns, d, k).ws_bytes;
+    // packed tensor path: one pass's workspace, whatever nq
+    const bool packed = k <= MMA_K_MAX && mma_packed_supported(ns, d, k);
+    if ((path == EVP_PATH_MMA_PACKED && packed) ||
+        (path == EVP_PATH_AUTO && packed && nq > EVP_AUTO_POPC_MAX_NQ))
+        best = std::max(best, mma_packed_workspace(ns, d, k));
     // tensor path, taken by AUTO from nq0 queries up: the slice count depends
     // on the number of query tiles, so the lists can need more room at fewer
     // queries; the largest call in each tile count is the last one
-    const int64_t nq0 = path == EVP_PATH_MMA ? 1 : auto_mma_min_nq(!convert_db);
+    const int64_t nq0 = path == EVP_PATH_MMA ? 1
+                        : packed             ? auto_packed_max_nq(!convert_db) + 1
+                                             : auto_mma_min_nq(!convert_db);
     if ((path == EVP_PATH_MMA || path == EVP_PATH_AUTO) && k <= MMA_K_MAX && nq >= nq0) {
         const int64_t qa = mma_active_queries(k);
         for (int64_t t = (nq0 + qa - 1) / qa; t <= (nq + qa - 1) / qa; ++t)
@@ -156,10 +170,12 @@ namespace {
 
 int32_t check_knn_args(int64_t nq, int64_t ns, int32_t d, int32_t x, int32_t k, int32_t path) {
     if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
-        (int64_t)k > ns || path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
+        (int64_t)k > ns || path < EVP_PATH_AUTO || path > EVP_PATH_MMA_PACKED)
         return EVP_ERR_INVALID;
     if (d > EVP_MAX_D_SCAN || k > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
-    if (resolve_path(nq, k, path) == EVP_PATH_MMA && k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
+    const int rp = resolve_path(nq, ns, d, k, path);
+    if (rp == EVP_PATH_MMA && k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
+    if (rp == EVP_PATH_MMA_PACKED && !mma_packed_supported(ns, d, k)) return EVP_ERR_UNSUPPORTED;
     return EVP_OK;
 }
 
@@ -186,8 +202,11 @@ int32_t ternary_knn_path(const uint64_t* Q, int64_t nq, const uint64_t* S, int64
     if ((reinterpret_cast<uintptr_t>(S) & 15) != 0 || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
         return EVP_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (resolve_path(nq, k, path) == EVP_PATH_MMA)
+    const int rp = resolve_path(nq, ns, d, k, path);
+    if (rp == EVP_PATH_MMA)
         return run_mma_knn(Q, nq, nullptr, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status, s);
+    if (rp == EVP_PATH_MMA_PACKED)
+        return run_mma_packed_knn(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status, s);
     return run_popc_knn(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status, s);
 }
 

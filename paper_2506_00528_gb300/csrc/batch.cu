@@ -2,7 +2,7 @@
 // resident databases, planned once and run as one CUDA graph.
 //
 // evp_batch_plan_create validates a list of batch descriptors, picks the
-// scan path of every batch from the autotuner's table (timing both paths on
+// scan path of every batch from the autotuner's table (timing the paths on
 // first sight of a (database, query-count bucket, k) class, see
 // evp_autotune), sizes one workspace per batch and allocates them together.
 // evp_batch_run enqueues every batch on the caller's stream, spreading
@@ -85,9 +85,12 @@ int32_t evp_autotune(evp_db_t db, int64_t nq, int32_t k, int32_t* path_out, floa
     // trial queries: the database's own first rows (the timing does not
     // depend on the query values)
     const uint64_t* Q = evp_db_codes(db);
-    const size_t ws_p = evp_db_knn_workspace(db, tq, k, EVP_PATH_POPC);
-    const size_t ws_m = k <= evp::MMA_K_MAX ? evp_db_knn_workspace(db, tq, k, EVP_PATH_MMA) : 0;
-    const size_t ws_bytes = std::max(ws_p, ws_m);
+    const bool packed = k <= evp::MMA_K_MAX && evp::mma_packed_supported(ns, d, k);
+    size_t wsz[4] = {0, 0, 0, 0};
+    wsz[EVP_PATH_POPC] = evp_db_knn_workspace(db, tq, k, EVP_PATH_POPC);
+    if (k <= evp::MMA_K_MAX) wsz[EVP_PATH_MMA] = evp_db_knn_workspace(db, tq, k, EVP_PATH_MMA);
+    if (packed) wsz[EVP_PATH_MMA_PACKED] = evp_db_knn_workspace(db, tq, k, EVP_PATH_MMA_PACKED);
+    const size_t ws_bytes = std::max({wsz[1], wsz[2], wsz[3]});
     void* ws = nullptr;
     int64_t* ids = nullptr;
     int32_t* dist = nullptr;
@@ -102,15 +105,15 @@ int32_t evp_autotune(evp_db_t db, int64_t nq, int32_t k, int32_t* path_out, floa
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float t[3] = {0.f, 1e30f, 1e30f};
+    float t[4] = {0.f, 1e30f, 1e30f, 1e30f};
     int32_t rc = EVP_OK;
-    for (int path = EVP_PATH_POPC; path <= EVP_PATH_MMA && rc == EVP_OK; ++path) {
-        if (path == EVP_PATH_MMA && k > evp::MMA_K_MAX) break;
-        const size_t wsz = path == EVP_PATH_POPC ? ws_p : ws_m;
+    for (int path = EVP_PATH_POPC; path <= EVP_PATH_MMA_PACKED && rc == EVP_OK; ++path) {
+        if (path != EVP_PATH_POPC && k > evp::MMA_K_MAX) break;
+        if (path == EVP_PATH_MMA_PACKED && !packed) break;
         // one warm-up, then the timed run
         for (int rep = 0; rep < 2 && rc == EVP_OK; ++rep) {
             cudaEventRecord(e0, s);
-            rc = evp_db_knn(db, Q, tq, k, ids, dist, ws, wsz, nullptr, stream, path);
+            rc = evp_db_knn(db, Q, tq, k, ids, dist, ws, wsz[path], nullptr, stream, path);
             cudaEventRecord(e1, s);
         }
         if (rc == EVP_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&t[path], e0, e1);
@@ -120,16 +123,17 @@ int32_t evp_autotune(evp_db_t db, int64_t nq, int32_t k, int32_t* path_out, floa
     cudaFree(ws);
     cudaFree(ids);
     cudaFree(dist);
-    (void)d;
     if (rc != EVP_OK) return rc;
-    const int32_t best = t[EVP_PATH_MMA] < t[EVP_PATH_POPC] ? EVP_PATH_MMA : EVP_PATH_POPC;
+    int32_t best = EVP_PATH_POPC;
+    for (int path = EVP_PATH_MMA; path <= EVP_PATH_MMA_PACKED; ++path)
+        if (t[path] < t[best]) best = path;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         g_tune[key] = best;
     }
     *path_out = best;
     if (popc_ms) *popc_ms = t[EVP_PATH_POPC];
-    if (mma_ms) *mma_ms = t[EVP_PATH_MMA];
+    if (mma_ms) *mma_ms = std::min(t[EVP_PATH_MMA], t[EVP_PATH_MMA_PACKED]);
     return EVP_OK;
 }
 

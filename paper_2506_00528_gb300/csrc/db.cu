@@ -21,10 +21,7 @@ namespace {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 int resolve_db_path(const evp_db* db, int64_t nq, int32_t k, int32_t path) {
-    if (path == EVP_PATH_AUTO)
-        return (nq >= auto_mma_min_nq(db->S8 != nullptr) && k <= MMA_K_MAX) ? EVP_PATH_MMA
-                                                                              : EVP_PATH_POPC;
-    return path;
+    return path == EVP_PATH_AUTO ? auto_path(nq, db->ns, db->d, k, db->S8 != nullptr) : path;
 }
 
 size_t db_knn_ws(const evp_db* db, int64_t nq, int32_t k, int32_t path) {
@@ -112,11 +109,14 @@ int32_t evp_db_knn(evp_db_t db, const uint64_t* Q, int64_t nq, int32_t k, int64_
                    int32_t* dist, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream,
                    int32_t path) {
     if (!db) return EVP_ERR_INVALID;
-    if (nq < 0 || k < 1 || (int64_t)k > db->ns || path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
+    if (nq < 0 || k < 1 || (int64_t)k > db->ns || path < EVP_PATH_AUTO ||
+        path > EVP_PATH_MMA_PACKED)
         return EVP_ERR_INVALID;
     if (k > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
     const int rp = resolve_db_path(db, nq, k, path);
     if (rp == EVP_PATH_MMA && k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
+    if (rp == EVP_PATH_MMA_PACKED && !mma_packed_supported(db->ns, db->d, k))
+        return EVP_ERR_UNSUPPORTED;
     if (nq == 0) return EVP_OK;
     if (!Q || !ids || !dist || !ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0)
         return EVP_ERR_INVALID;
@@ -124,6 +124,9 @@ int32_t evp_db_knn(evp_db_t db, const uint64_t* Q, int64_t nq, int32_t k, int64_
     if (rp == EVP_PATH_MMA)
         return run_mma_knn(Q, nq, db->S8, db->T, db->ns, db->d, db->x, k, ids, dist, ws, ws_bytes,
                            dev_status, s);
+    if (rp == EVP_PATH_MMA_PACKED)
+        return run_mma_packed_knn(Q, nq, db->T, db->ns, db->d, db->x, k, ids, dist, ws, ws_bytes,
+                                  dev_status, s);
     return run_popc_knn(Q, nq, db->T, db->ns, db->d, db->x, k, ids, dist, ws, ws_bytes,
                         dev_status, s);
 }
@@ -143,7 +146,7 @@ int32_t evp_db_search_path(evp_db_t db, const float* Q, int64_t nq, int32_t n_sh
                            int32_t* dev_status, void* stream, int32_t path) {
     if (!db) return EVP_ERR_INVALID;
     if (nq < 0 || k < 1 || n_shortlist < k || (int64_t)n_shortlist > db->ns ||
-        path < EVP_PATH_AUTO || path > EVP_PATH_MMA)
+        path < EVP_PATH_AUTO || path > EVP_PATH_MMA_PACKED)
         return EVP_ERR_INVALID;
     if (n_shortlist > EVP_MAX_K) return EVP_ERR_UNSUPPORTED;
     if (nq == 0) return EVP_OK;

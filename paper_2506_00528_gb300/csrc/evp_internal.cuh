@@ -61,6 +61,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// One arrival on a barrier of this CTA.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Wait for the phase with the given parity; give up after WAIT_LIMIT_NS.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
     if (mbar_try_wait(bar, parity)) return true;
@@ -83,28 +88,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
-// ---- warp-level sorted-key helpers -------------------------------------
-// Ascending bitonic sort of buf[0, P) (P a power of two) by one warp.
-__device__ __forceinline__ void warp_bitonic_sort(uint64_t* buf, int P) {
-    const int lane = threadIdx.x & 31;
-    for (int kk = 2; kk <= P; kk <<= 1) {
-        for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int i = lane; i < P; i += 32) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const uint64_t a = buf[i], b = buf[ixj];
-                    const bool up = (i & kk) == 0;
-                    if ((a > b) == up) {
-                        buf[i] = b;
-                        buf[ixj] = a;
-                    }
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
+// ---- sorted-key and team helpers ------------------------------------
 // Number of entries of the ascending array a[0, n) that are < key.
 __device__ __forceinline__ int lower_bound_u64(const uint64_t* a, int n, uint64_t key) {
     int lo = 0, hi = n;
@@ -116,25 +100,117 @@ __device__ __forceinline__ int lower_bound_u64(const uint64_t* a, int n, uint64_
     return lo;
 }
 
-// out[0, min(k, nL + nc)) = the smallest keys of L[0,nL) and C[0,nc), both
-// ascending with all keys distinct.  One warp; out must not alias L or C.
-// Returns the new length.
-__device__ __forceinline__ int warp_merge_topk(const uint64_t* L, int nL, const uint64_t* C,
-                                               int nc, uint64_t* out, int k) {
-    const int lane = threadIdx.x & 31;
-    for (int i = lane; i < nL; i += 32) {
-        const uint64_t key = L[i];
-        const int r = i + lower_bound_u64(C, nc, key);
-        if (r < k) out[r] = key;
+__device__ inline int next_pow2(int v) {
+    int p = 32;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+__device__ __forceinline__ void named_barrier(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+// The smallest bin T with sum(hist[0..T]) >= k, scanning up from the
+// smallest non-empty bin; 0xFFFFFFFF if fewer than k keys are counted.
+// Team-wide (every thread gets the result); `scratch` holds TT/32 + 2 words.
+template <typename Sync>
+__device__ __forceinline__ uint32_t team_kth_bin(const uint32_t* hist, const uint32_t* minhalf,
+                                                 int bins, uint32_t k, uint32_t* scratch, int t,
+                                                 int TT, Sync& sync) {
+    const int nw = TT / 32, wt = t >> 5, ln = t & 31;
+    if (t == 0) {
+        scratch[nw] = __ldcg(minhalf);
+        scratch[nw + 1] = 0xFFFFFFFFu;
     }
-    for (int j = lane; j < nc; j += 32) {
-        const uint64_t key = C[j];
-        const int r = j + lower_bound_u64(L, nL, key);
-        if (r < k) out[r] = key;
+    sync();
+    const uint32_t lo = scratch[nw];
+    uint32_t before = 0, T = 0xFFFFFFFFu;
+    for (uint32_t h0 = lo; h0 < (uint32_t)bins; h0 += (uint32_t)TT) {
+        const uint32_t h = h0 + (uint32_t)t;
+        const uint32_t c = h < (uint32_t)bins ? __ldcg(&hist[h]) : 0u;
+        uint32_t sum = c;  // inclusive scan over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t n = __shfl_up_sync(0xffffffffu, sum, o);
+            if (ln >= o) sum += n;
+        }
+        if (ln == 31) scratch[wt] = sum;
+        sync();
+        uint32_t off = 0, total = 0;
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t v = scratch[w];
+            if (w < wt) off += v;
+            total += v;
+        }
+        sum += off;
+        if (c > 0 && before + sum >= k && before + sum - c < k) scratch[nw + 1] = h;
+        sync();
+        T = scratch[nw + 1];
+        before += total;
+        if (T != 0xFFFFFFFFu || before >= k) break;
     }
-    __syncwarp();
-    const int total = nL + nc;
-    return total < k ? total : k;
+    return T;
+}
+
+// ---- tcgen05 / TMEM ----------------------------------------------------
+// Shared-memory matrix descriptor of a K-major SWIZZLE_128B tile whose
+// 8-row core groups are 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4)  // start address
+           | (1ull << 16)                       // leading byte offset (unused for SW128 K-major)
+           | (64ull << 32)                      // stride byte offset 1024 >> 4
+           | (1ull << 46)                       // descriptor version
+           | (2ull << 61);                      // SWIZZLE_128B
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Bounded mbarrier wait that also gives up as soon as *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity,
+                                                   const int* abort) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*reinterpret_cast<const volatile int*>(abort)) return false;
+        if (globaltimer_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return true;
+}
+
+// Issue a 32-column TMEM load without waiting for it.
+__device__ __forceinline__ void tmem_ld32_async(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+}
+
+// Wait for the warp's outstanding TMEM loads; v is an in-out operand so that
+// no use of the loaded registers can be scheduled before the wait.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+          "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]),
+          "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]),
+          "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+          "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]),
+          "+r"(v[31])
+        :
+        : "memory");
 }
 
 // ---- kernel timing (measurement support) ------------------------------
@@ -205,6 +281,13 @@ constexpr int MMA_K_MAX = 1024;  // largest k of the tensor-core path
 // then reads 1 byte per element at HBM speed, faster than a 16-query
 // popcount pass), from 17 when the copy must be built first.
 inline int64_t auto_mma_min_nq(bool resident_copy) { return resident_copy ? 9 : 17; }
+// Largest query count for which the automatic choice takes the packed
+// tensor-core scan (where it applies): one 64-query pass costs about what
+// the e4m3 scan costs against a resident copy; without one, the e4m3 scan
+// must first expand the whole database.
+inline int64_t auto_packed_max_nq(bool resident_copy) {
+    return resident_copy ? EVP_AUTO_PACKED_MAX_NQ : EVP_AUTO_PACKED_MAX_NQ_NO_COPY;
+}
 int mma_kp(int d);
 // Workspace bytes that serve every kNN call with at most nq queries (and
 // the same other arguments) on `path` (AUTO resolved per call).
@@ -220,6 +303,18 @@ cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
 int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint64_t* S,
                     int64_t ns, int d, int x, int k, int64_t* ids, int32_t* dist, void* ws,
                     size_t ws_bytes, int32_t* status, cudaStream_t stream);
+
+// Packed tensor-core path (database rows as the MMA's M side, tiles
+// unpacked on chip).  supported(): d, k and ns within its limits.
+bool mma_packed_supported(int64_t ns, int d, int k);
+size_t mma_packed_workspace(int64_t ns, int d, int k);
+int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
+                           int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
+                           int32_t* status, cudaStream_t stream);
+
+// Path the automatic rule takes for nq queries (resident_copy: the
+// database's e4m3 copy is resident).
+int auto_path(int64_t nq, int64_t ns, int d, int k, bool resident_copy);
 
 cudaError_t launch_rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int d,
                           const int64_t* shortlist, int n, int k, int64_t* ids, float* scores,

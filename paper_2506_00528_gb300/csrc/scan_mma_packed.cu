@@ -1,0 +1,862 @@
+// ternary_knn, packed tensor-core path: the exhaustive scan of Sec. 5.3 as
+// a dense contraction on the tensor cores (tcgen05, kind::f8f6f4) that
+// reads the packed 2-bit codes straight from HBM and unpacks each tile on
+// chip, for batches of up to 64 queries per pass.
+//
+// D = S Q^T with the database tile as the M side (128 rows = the 128 TMEM
+// lanes) and the pass's queries as the N side (16, 32 or 64):
+//   * database element of a code: +1 -> e4m3 0x40 (+2), -1 -> 0xC0 (-2),
+//     0 -> 0x00; query element: +1 -> 0x38 (+1), -1 -> 0xB8 (-1).  Every
+//     product is 0 or +-2 and float32 accumulation of at most 2d of them is
+//     exact, so D = 2 b2sp (Sec. 5.1.2) and Delta = 2x - D for codes with
+//     x non-zeros each;
+//   * the K order of both operands is the same permutation of the
+//     dimensions (a scalar product does not depend on the order of its
+//     terms): within each 32-dimension half of a 64-bit word, K position
+//     4j + b (j = 0..7, b = 0..3) holds dimension 8b + j.  Then the four
+//     bytes of one 32-bit TMEM column are bits j, 8 + j, 16 + j and 24 + j
+//     of the two bitplanes, and a column is two shifts and masks of a word
+//     in which the non-zero bit of each dimension sits next to its sign bit.
+//
+// Kernel (one CTA per SM, persistent over a contiguous slice of 128-row
+// tiles, 480 threads in five roles that meet only at mbarriers):
+//   warp 13     TMA producer: tiles of packed rows (box 2W + 2 words wide,
+//               the padding words read as 0 so that 16-byte row reads are
+//               bank-conflict free) through a ring of mbarrier stages;
+//   warps 0-7   unpack, two threads per database row (TMEM lane): each
+//               copies its half of the row's 16-byte word pairs out of the
+//               stage, releases the stage and writes the unpacked e4m3
+//               columns with tcgen05.st into one of two A buffers (192
+//               columns each) once the MMAs have read it;
+//   warp 12     allocates the 512 TMEM columns and issues the MMAs from one
+//               thread: A (the unpacked tile) from TMEM, B (the queries)
+//               from shared memory (SWIZZLE_128B, written once at start),
+//               D into one of two accumulators (QN columns each);
+//   warps 8-11  epilogue, one thread per row: reads the row's QN
+//               accumulator columns, and appends rows that beat a query's
+//               threshold to that query's candidate buffer in shared memory;
+//               the four warps merge full buffers (bitonic sort + merge
+//               path) into per-(query, slice) sorted lists of the k best in
+//               the workspace;
+//   warp 14     union-bound helper: per query, the k-th smallest Delta/2
+//               over every row any slice has appended, from a histogram in
+//               the workspace that all slices share; the epilogue folds it
+//               (and the other slices' list thresholds) into its own.
+// The per-query final merge of the popcount path combines the lists.
+// Every mbarrier wait is bounded (2 s): on expiry the CTA reports
+// EVP_ERR_TIMEOUT, raises its abort flag (every other wait then gives up at
+// once), waits for the copies and MMAs it issued and frees TMEM.
+#include "evp_internal.cuh"
+
+#include <algorithm>
+
+namespace evp {
+
+namespace {
+
+constexpr int PK_ROWS = 128;                         // database rows per tile = TMEM lanes
+constexpr int PK_UNPACK_WARPS = 8;                   // warps 0-7: two threads per row
+constexpr int PK_EPI_WARP0 = 8;                      // warps 8-11: one thread per row
+constexpr int PK_EPI_WARPS = 4;
+constexpr int PK_EPI_THREADS = PK_EPI_WARPS * 32;
+constexpr int PK_MMA_WARP = 12;
+constexpr int PK_TMA_WARP = 13;
+constexpr int PK_HELPER_WARP = 14;
+constexpr int PK_THREADS = 15 * 32;
+constexpr int PK_STAGE_LIST_K = 128;                 // merges stage the list in shared memory up to this k
+constexpr int PK_QN_MAX = 64;                        // queries per pass
+constexpr int PK_W_MAX = 12;                         // words per bitplane: d <= 768
+constexpr int PK_CAP = 256;                          // candidate slots per query
+constexpr int PK_MERGE_AT = PK_CAP - PK_ROWS;        // merge at this count: a tile adds <= PK_ROWS
+constexpr int PK_LOCAL_BITS = 20;                    // row-in-slice bits of a candidate key
+constexpr int64_t PK_MAX_TILES_PER_SLICE = (int64_t(1) << PK_LOCAL_BITS) / PK_ROWS;
+constexpr int PK_MAX_STAGES = 6;
+constexpr int PK_MIN_STAGES = 2;
+constexpr int PK_SMEM_LIMIT = 232448;                // opt-in shared memory per block
+constexpr uint32_t PK_TMEM_COLS = 512;
+constexpr int PK_A_COLS = 16 * PK_W_MAX;             // 192: one unpacked tile (768 K bytes)
+constexpr int PK_D_COL0 = 2 * PK_A_COLS;             // accumulators after the two A buffers
+constexpr int PK_MAX_SLICES = 1024;                  // lists the final merge takes per query
+static_assert(PK_D_COL0 + 2 * PK_QN_MAX <= (int)PK_TMEM_COLS, "TMEM columns");
+
+struct PkArgs {
+    const uint64_t* Q;     // this pass's query codes [nqg][2W]
+    int nqg;
+    int64_t ns;
+    int W;                 // words per bitplane (even, <= PK_W_MAX)
+    int x, k;
+    int pitch;             // uint64 words per staged row (2W + 2)
+    int stages;
+    int64_t tiles_per_slice, ntiles;
+    uint64_t* lists;       // [PK_QN_MAX][nslices][2][k]
+    int32_t* meta;         // [PK_QN_MAX][nslices][2]: (length, current buffer)
+    uint64_t* tau_global;  // [PK_QN_MAX]
+    uint32_t* hist;        // [PK_QN_MAX][hist_bins]
+    uint32_t* minhalf;     // [PK_QN_MAX]
+    int hist_bins;         // 2x + 1
+    int32_t* status;
+};
+
+__host__ __device__ inline size_t pk_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct PkLayout {
+    size_t stage_bytes, b_off, cand_off, scratch_off, tau_off, thr_off, ub_off, cnt_off, bar_off,
+        misc_off, total;
+};
+
+// Shared-memory carve-up (offsets from a 1024-byte aligned base; `total`
+// includes the alignment slack of the dynamic allocation).
+__host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn) {
+    PkLayout L;
+    L.stage_bytes = pk_align((size_t)PK_ROWS * (2 * W + 2) * 8, 1024);
+    L.b_off = L.stage_bytes * stages;
+    L.cand_off = L.b_off + (size_t)(W / 2) * qn * 128;  // W/2 K-chunks of qn x 128 B
+    L.scratch_off = L.cand_off + (size_t)qn * PK_CAP * 4;  // one staged list per epilogue warp
+    L.tau_off = L.scratch_off + (size_t)PK_EPI_WARPS * PK_STAGE_LIST_K * 8;
+    L.thr_off = L.tau_off + (size_t)qn * 8;
+    L.ub_off = L.thr_off + (size_t)qn * 4;
+    L.cnt_off = L.ub_off + (size_t)qn * 4;
+    L.bar_off = pk_align(L.cnt_off + (size_t)4 * qn * 4, 8);
+    L.misc_off = L.bar_off + (size_t)(2 * stages + 6) * 8;
+    L.total = L.misc_off + 16 + 1024;
+    return L;
+}
+
+// Instruction descriptor: D = f32, A = B = e4m3, both K-major, M = 128, N = qn.
+__host__ __device__ constexpr uint32_t pk_idesc(int qn) {
+    return (1u << 4) | ((uint32_t)(qn >> 3) << 17) | ((uint32_t)(PK_ROWS >> 4) << 24);
+}
+
+// D (TMEM) += A (TMEM) * B (shared memory descriptor).
+__device__ __forceinline__ void mma_f8_tmem_a(uint32_t dtmem, uint32_t atmem, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(dtmem),
+        "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+// Store 32 consecutive 32-bit columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(
+            taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]),
+        "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]),
+        "r"(v[29]), "r"(v[30]), "r"(v[31])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Load N (8, 16 or 32) consecutive 32-bit columns of this warp's lanes and
+// wait for them.
+template <int N>
+__device__ __forceinline__ void tmem_ld_wait(uint32_t taddr, uint32_t (&v)[N]) {
+    if constexpr (N == 32) {
+        tmem_ld32_async(taddr, v);
+        tmem_wait_ld(v);
+    } else if constexpr (N == 16) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+            "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr)
+            : "memory");
+    } else {
+        static_assert(N == 8, "8, 16 or 32 columns");
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n\t"
+            "tcgen05.wait::ld.sync.aligned;"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7])
+            : "r"(taddr)
+            : "memory");
+    }
+}
+
+// Named barrier over `n` threads that also returns whether any of them
+// passed p = true.
+__device__ __forceinline__ bool bar_red_or(int id, int n, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\t"
+        "setp.ne.u32 pi, %3, 0;\n\t"
+        "bar.red.or.pred po, %1, %2, pi;\n\t"
+        "selp.u32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"(id), "r"(n), "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
+// TMEM columns of one 64-bit word pair of the bitplanes (64 dimensions per
+// word, 16 columns each; see the K order above).  nz = v+ | v-, ng = v-.
+// The database byte of a dimension is (nz << 6) | (ng << 7).
+__device__ __forceinline__ void unpack_half(uint32_t nz, uint32_t ng, uint32_t* o) {
+    constexpr uint32_t M = 0xC0C0C0C0u;
+    const uint32_t rng = __funnelshift_l(ng, ng, 1);  // sign of dimension i at bit i + 1
+    const uint32_t xe = (nz & 0x55555555u) | (rng & 0xAAAAAAAAu);
+    const uint32_t xo = (nz & 0xAAAAAAAAu) | (rng & 0x55555555u);
+    o[0] = (xe << 6) & M;
+    o[1] = (xo << 5) & M;
+    o[2] = (xe << 4) & M;
+    o[3] = (xo << 3) & M;
+    o[4] = (xe << 2) & M;
+    o[5] = (xo << 1) & M;
+    o[6] = xe & M;
+    o[7] = __funnelshift_r(xo, xo, 1) & M;
+}
+
+__device__ __forceinline__ void unpack_word(uint64_t p, uint64_t m, uint32_t* o) {
+    const uint64_t nz = p | m;
+    unpack_half((uint32_t)nz, (uint32_t)m, o);
+    unpack_half((uint32_t)(nz >> 32), (uint32_t)(m >> 32), o + 8);
+}
+
+// Candidate key (Delta/2 << 20 | row - row0) -> list key (Delta << 32 | row).
+__device__ __forceinline__ uint64_t pk_key64(uint32_t c, int64_t row0) {
+    return ((uint64_t)(2u * (c >> PK_LOCAL_BITS)) << 32) |
+           (uint64_t)(row0 + (int64_t)(c & ((1u << PK_LOCAL_BITS) - 1u)));
+}
+
+__device__ __forceinline__ int lower_bound_cand(const uint32_t* C, int n, uint64_t key,
+                                                int64_t row0) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pk_key64(C[mid], row0) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Ascending bitonic sort of buf[0, P) (P a power of two) by one warp.
+__device__ __forceinline__ void warp_sort_u32(uint32_t* buf, int P, int lane) {
+    for (int kk = 2; kk <= P; kk <<= 1) {
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = lane; i < P; i += 32) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint32_t x0 = buf[i], x1 = buf[ixj];
+                    if ((x0 > x1) == ((i & kk) == 0)) {
+                        buf[i] = x1;
+                        buf[ixj] = x0;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Admission threshold on D for a query threshold key tau = (Delta << 32 |
+// row): D > thr admits exactly Delta <= Delta(tau) (the exact key test
+// follows on the rare candidates).  No threshold yet: -2^22, below every D
+// and small enough that D - thr stays exact in float32.
+constexpr float PK_ADMIT_ALL = -4194304.0f;
+__device__ __forceinline__ float pk_thr(uint64_t tau, int x) {
+    if (tau == KEY_NONE) return PK_ADMIT_ALL;
+    return (float)(2 * x - (int)(tau >> 32)) - 0.5f;
+}
+
+template <int QN>
+__global__ void __launch_bounds__(PK_THREADS, 1)
+scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a) {
+    constexpr uint32_t IDESC = pk_idesc(QN);
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+    const int W = a.W, k = a.k, x = a.x, S = a.stages;
+    const PkLayout L = pk_layout(W, S, QN);
+    uint8_t* stages = smem;
+    uint8_t* qop = smem + L.b_off;  // query operand, W/2 chunks of QN x 128 B
+    uint32_t* cand = reinterpret_cast<uint32_t*>(smem + L.cand_off);
+    uint64_t* scratch = reinterpret_cast<uint64_t*>(smem + L.scratch_off);
+    uint64_t* tau = reinterpret_cast<uint64_t*>(smem + L.tau_off);
+    float* thr_s = reinterpret_cast<float*>(smem + L.thr_off);
+    uint32_t* ub = reinterpret_cast<uint32_t*>(smem + L.ub_off);
+    int* cnt = reinterpret_cast<int*>(smem + L.cnt_off);
+    int* len = cnt + QN;
+    int* cur = len + QN;
+    uint32_t* lmin = reinterpret_cast<uint32_t*>(cur + QN);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
+    uint64_t* full = bars;                 // [S]  TMA -> unpack warps
+    uint64_t* empty = bars + S;            // [S]  unpack warps -> TMA
+    uint64_t* a_full = bars + 2 * S;       // [2]  unpack warps -> MMA (A buffer written)
+    uint64_t* d_full = bars + 2 * S + 2;   // [2]  MMA -> epilogue and unpack warps (tile's
+                                           //      MMAs complete: accumulator ready, A read)
+    uint64_t* d_empty = bars + 2 * S + 4;  // [2]  epilogue -> MMA (accumulator read)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    int* epi_bad = abort_flag + 1;         // an epilogue warp gave up on a wait
+    int* epi_done = abort_flag + 2;        // the epilogue finished (the helper stops)
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nslices = gridDim.x, slice = blockIdx.x;
+    const int64_t tile0 = (int64_t)slice * a.tiles_per_slice;
+    const int64_t tile_end = min(tile0 + a.tiles_per_slice, a.ntiles);
+    const int ntl = tile_end > tile0 ? (int)(tile_end - tile0) : 0;
+    const int64_t row0 = tile0 * PK_ROWS;
+    const int npairs = W / 2;
+    const int ksteps = 2 * W;  // K = 64 W bytes, 32 per MMA
+    const uint32_t tile_bytes = (uint32_t)(PK_ROWS * a.pitch * 8);
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], PK_UNPACK_WARPS);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&a_full[b], PK_UNPACK_WARPS);
+            mbar_init(&d_full[b], 1);
+            mbar_init(&d_empty[b], PK_EPI_WARPS);
+        }
+        *abort_flag = 0;
+        *epi_bad = 0;
+        *epi_done = 0;
+        fence_mbar_init();
+    }
+    // Query operand: 16-byte units of K-major SWIZZLE_128B rows (the 16-byte
+    // unit u of row n of a 128-byte chunk sits at unit u ^ (n % 8)).
+    {
+        const int units_per_row = 4 * W;  // 64 W bytes / 16
+        for (int i = tid; i < QN * units_per_row; i += PK_THREADS) {
+            const int n = i / units_per_row, ku = i - n * units_per_row;
+            const int kb0 = ku * 16;
+            uint32_t o[4] = {0u, 0u, 0u, 0u};
+            if (n < a.nqg) {
+                const int w = kb0 >> 6;
+                const uint64_t p = a.Q[(int64_t)n * 2 * W + w];
+                const uint64_t m = a.Q[(int64_t)n * 2 * W + W + w];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int s = (kb0 & 63) + e;  // K position within the word
+                    const int bit = 32 * (s >> 5) + 8 * (s & 3) + ((s & 31) >> 2);
+                    const uint32_t byte = ((p >> bit) & 1u) ? 0x38u : (((m >> bit) & 1u) ? 0xB8u : 0u);
+                    o[e >> 2] |= byte << (8 * (e & 3));
+                }
+            }
+            const int c = kb0 >> 7, uc = (kb0 & 127) >> 4;
+            uint8_t* dst = qop + (size_t)c * QN * 128 + (n >> 3) * 1024 + (n & 7) * 128 +
+                           ((uc ^ (n & 7)) << 4);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes read by the tensor core
+    }
+    if (tid < QN) {
+        tau[tid] = KEY_NONE;
+        thr_s[tid] = tid < a.nqg ? PK_ADMIT_ALL : INFINITY;  // padding queries never admit
+        ub[tid] = 0xFFFFFFFFu;
+        cnt[tid] = 0;
+        len[tid] = 0;
+        cur[tid] = 0;
+        lmin[tid] = 0xFFFFFFFFu;
+    }
+    if (warp == PK_MMA_WARP) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(PK_TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    auto give_up = [&]() {
+        if (!*(volatile int*)abort_flag) report(a.status, EVP_ERR_TIMEOUT);
+        *(volatile int*)abort_flag = 1;
+    };
+
+    if (warp == PK_TMA_WARP) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            bool ok = true;
+            int t = 0;
+            for (; t < ntl; ++t) {
+                const int s = t % S;
+                if (t >= S &&
+                    !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / S) - 1) & 1), abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], tile_bytes);
+                tma_load_2d(stages + (size_t)s * L.stage_bytes, &tmap, &full[s], 0,
+                            (int32_t)((tile0 + t) * PK_ROWS));
+            }
+            // every copy issued has landed before the CTA can exit: the last
+            // S stages' releases (or, after an abort, their arrivals)
+            for (int j = max(0, t - S); j < t; ++j) {
+                const int s = j % S;
+                if (ok) ok = mbar_wait_or_abort(&empty[s], (uint32_t)((j / S) & 1), abort_flag);
+                if (!ok) mbar_wait_bounded(&full[s], (uint32_t)((j / S) & 1));
+            }
+            if (!ok) give_up();
+        }
+    } else if (warp == PK_MMA_WARP) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            // descriptors of the K steps differ only in the start address
+            // field (16-byte units): chunk kk / 4 of QN x 128 B, 32 B per step;
+            // all computed once, so that the loop issues little besides MMAs
+            const uint64_t bdesc0 = sw128_desc(smem_u32(qop));
+            uint64_t bd[2 * PK_W_MAX];
+#pragma unroll
+            for (int kk = 0; kk < 2 * PK_W_MAX; ++kk)
+                bd[kk] = bdesc0 + (uint64_t)((kk >> 2) * QN * 8 + (kk & 3) * 2);
+            bool ok = true;
+            for (int t = 0; t < ntl && ok; ++t) {
+                const int b = t & 1;
+                const uint32_t use = (uint32_t)(t >> 1);
+                if (!mbar_wait_or_abort(&a_full[b], use & 1u, abort_flag) ||
+                    !mbar_wait_or_abort(&d_empty[b], (use & 1u) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dt = tmem_base + (uint32_t)(PK_D_COL0 + b * QN);
+                const uint32_t at = tmem_base + (uint32_t)(b * PK_A_COLS);
+                mma_f8_tmem_a(dt, at, bd[0], IDESC, 0u);
+#pragma unroll
+                for (int kk = 1; kk < 2 * PK_W_MAX; ++kk)
+                    if (kk < ksteps) mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk], IDESC, 1u);
+                mma_commit(&d_full[b]);  // one commit per tile: each drains the MMA pipe
+            }
+            if (!ok) give_up();
+        }
+    } else if (warp < PK_UNPACK_WARPS) {
+        // ---------------- unpack warps ----------------
+        const int h = warp >> 2;               // word pairs h, h + 2, ... of the row
+        const int r = (warp & 3) * 32 + lane;  // row in the tile = TMEM lane
+        const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        for (int t = 0; t < ntl; ++t) {
+            const int s = t % S, b = t & 1;
+            int got = 1;
+            if (lane == 0) got = mbar_wait_or_abort(&full[s], (uint32_t)((t / S) & 1), abort_flag);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                if (lane == 0) give_up();
+                break;
+            }
+            const uint64_t* rp =
+                reinterpret_cast<const uint64_t*>(stages + (size_t)s * L.stage_bytes) +
+                (size_t)r * a.pitch;
+            ulonglong2 pw[PK_W_MAX / 4], mw[PK_W_MAX / 4];
+#pragma unroll
+            for (int i = 0; i < PK_W_MAX / 4; ++i) {
+                const int pi = h + 2 * i;
+                if (pi < npairs) {
+                    pw[i] = reinterpret_cast<const ulonglong2*>(rp)[pi];
+                    mw[i] = reinterpret_cast<const ulonglong2*>(rp + W)[pi];
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);
+            // the MMAs of tile t - 2 (the previous use of A buffer b) are complete;
+            // d_full[b] cannot complete again before this warp writes A(t)
+            if (lane == 0)
+                got = mbar_wait_or_abort(&d_full[b], (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                if (lane == 0) give_up();
+                break;
+            }
+            tc_fence_after();
+            const uint32_t abase = tmem_base + lane_off + (uint32_t)(b * PK_A_COLS);
+#pragma unroll
+            for (int i = 0; i < PK_W_MAX / 4; ++i) {
+                const int pi = h + 2 * i;
+                if (pi < npairs) {
+                    uint32_t o[32];
+                    unpack_word(pw[i].x, mw[i].x, o);
+                    unpack_word(pw[i].y, mw[i].y, o + 16);
+                    tmem_st32(abase + (uint32_t)(32 * pi), o);
+                }
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[b]);
+        }
+    } else if (warp < PK_EPI_WARP0 + PK_EPI_WARPS) {
+        // ---------------- epilogue warps ----------------
+        const int ew = warp - PK_EPI_WARP0;
+        const int r = ew * 32 + lane;  // row in the tile = TMEM lane (warp % 4 == ew)
+        const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
+        bool bad = false;      // this warp gave up on a wait
+        bool my_need = false;  // a candidate buffer this thread appended to needs a merge
+        for (int t = 0;; ++t) {
+            const bool fin = t == ntl;
+            if (!fin && !bad) {
+                const int b = t & 1;
+                int got = 1;
+                if (lane == 0)
+                    got = mbar_wait_or_abort(&d_full[b], (uint32_t)((t >> 1) & 1), abort_flag);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) {
+                    bad = true;
+                    if (lane == 0) {
+                        *(volatile int*)epi_bad = 1;
+                        give_up();
+                    }
+                } else {
+                    tc_fence_after();
+                    const int64_t row = (tile0 + t) * PK_ROWS + r;
+                    const uint32_t dcol = tmem_base + lane_off + (uint32_t)(PK_D_COL0 + b * QN);
+                    // chunks of QC accumulator columns (queries), the accumulator
+                    // released after the last chunk is read
+                    constexpr int QC = QN < 32 ? QN : 32;
+#pragma unroll
+                    for (int ci = 0; ci < QN / QC; ++ci) {
+                        uint32_t v[QC];
+                        tmem_ld_wait<QC>(dcol + (uint32_t)(ci * QC), v);
+                        if (ci == QN / QC - 1) {
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&d_empty[b]);
+                        }
+                        // D - threshold per query, then the largest of them (the
+                        // thresholds are finite half-integers, -2^22 or +inf:
+                        // D - threshold is exact and D = (D - threshold) + threshold)
+                        const float4* th4 = reinterpret_cast<const float4*>(thr_s + ci * QC);
+                        float gap = -INFINITY;
+#pragma unroll
+                        for (int c = 0; c < QC / 4; ++c) {
+                            const float4 th = th4[c];
+                            const float g0 = __uint_as_float(v[4 * c]) - th.x;
+                            const float g1 = __uint_as_float(v[4 * c + 1]) - th.y;
+                            const float g2 = __uint_as_float(v[4 * c + 2]) - th.z;
+                            const float g3 = __uint_as_float(v[4 * c + 3]) - th.w;
+                            v[4 * c] = __float_as_uint(g0);
+                            v[4 * c + 1] = __float_as_uint(g1);
+                            v[4 * c + 2] = __float_as_uint(g2);
+                            v[4 * c + 3] = __float_as_uint(g3);
+                            gap = fmaxf(gap, fmaxf(fmaxf(g0, g1), fmaxf(g2, g3)));
+                        }
+                        const bool live = gap > 0.f && row < a.ns;
+                        if (!__any_sync(0xffffffffu, live)) continue;
+                        uint32_t msk = 0;
+#pragma unroll
+                        for (int q = 0; q < QC; ++q)
+                            msk |= (live && __uint_as_float(v[q]) > 0.f ? 1u : 0u) << q;
+                        const uint32_t any = __reduce_or_sync(0xffffffffu, msk);
+#pragma unroll
+                        for (int qq = 0; qq < QC; ++qq) {
+                            if (!((any >> qq) & 1u)) continue;
+                            const int q = ci * QC + qq;
+                            // Delta = 2x - D lies in [0, 4x] for codes with x non-zeros;
+                            // clamped so that other codes cannot index outside the histogram
+                            const float dq = __uint_as_float(v[qq]) + thr_s[q];
+                            const uint32_t delta = (uint32_t)min(
+                                max(2 * x - __float2int_rn(dq), 0), 4 * x);
+                            bool c = (msk >> qq) & 1u;
+                            if (c) c = (((uint64_t)delta << 32) | (uint64_t)row) < tau[q];
+                            const uint32_t am = __ballot_sync(0xffffffffu, c);
+                            if (!am) continue;
+                            const int leader = __ffs(am) - 1;
+                            int pos0 = 0;
+                            if (lane == leader) pos0 = atomicAdd(&cnt[q], __popc(am));
+                            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+                            const uint32_t half = delta >> 1;
+                            if (c) {
+                                const int rank = __popc(am & ((1u << lane) - 1u));
+                                cand[q * PK_CAP + pos0 + rank] =
+                                    (half << PK_LOCAL_BITS) | (uint32_t)(row - row0);
+                                // each row is appended at most once: count it for the union bound
+                                atomicAdd(&a.hist[(int64_t)q * a.hist_bins + half], 1u);
+                            }
+                            const uint32_t wmin = __reduce_min_sync(0xffffffffu, c ? half : 0xFFFFFFFFu);
+                            if (lane == leader) {
+                                if (wmin < lmin[q]) {
+                                    atomicMin(&lmin[q], wmin);
+                                    atomicMin(&a.minhalf[q], wmin);
+                                }
+                                if (pos0 + __popc(am) >= PK_MERGE_AT) my_need = true;
+                            }
+                        }
+                    }
+                }
+            }
+            // One barrier per tile; merges, threshold folds, the end and an
+            // abort take a second phase that every epilogue thread enters.
+            __syncwarp();
+            const bool phase = bar_red_or(1, PK_EPI_THREADS, my_need || bad);
+            const bool fold = (t & 7) == 7;
+            if (phase || fin || fold) {
+                const bool ab = *(volatile int*)epi_bad != 0;
+                if (!ab) {
+                    if (fold) {
+                        // other slices' thresholds and the union bound, one query per lane
+                        for (int q = ew + PK_EPI_WARPS * lane; q < a.nqg; q += PK_EPI_THREADS) {
+                            uint64_t tq = min(tau[q],
+                                              *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
+                            const uint32_t T = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
+                            if (T != 0xFFFFFFFFu) tq = min(tq, (uint64_t)(2u * T + 1u) << 32);
+                            tau[q] = tq;
+                            thr_s[q] = pk_thr(tq, x);
+                        }
+                        __syncwarp();
+                    }
+                    for (int q = ew; q < QN; q += PK_EPI_WARPS) {
+                        const int nc = cnt[q];
+                        if (nc >= PK_MERGE_AT || (fin && nc > 0)) {
+                            uint32_t* C = cand + q * PK_CAP;
+                            const int P = next_pow2(nc);
+                            for (int i = nc + lane; i < P; i += 32) C[i] = 0xFFFFFFFFu;
+                            __syncwarp();
+                            warp_sort_u32(C, P, lane);
+                            uint64_t* base = a.lists + ((int64_t)q * nslices + slice) * 2 * k;
+                            const int c0 = cur[q], nL = len[q];
+                            const uint64_t* Lst = base + (int64_t)c0 * k;
+                            uint64_t* out = base + (int64_t)(c0 ^ 1) * k;
+                            if (k <= PK_STAGE_LIST_K) {
+                                // the list, read once, is searched in shared memory
+                                uint64_t* Ls = scratch + ew * PK_STAGE_LIST_K;
+                                for (int i = lane; i < nL; i += 32) Ls[i] = Lst[i];
+                                __syncwarp();
+                                Lst = Ls;
+                            }
+                            for (int i = lane; i < nL; i += 32) {
+                                const uint64_t key = Lst[i];
+                                const int rr = i + lower_bound_cand(C, nc, key, row0);
+                                if (rr < k) out[rr] = key;
+                            }
+                            for (int j = lane; j < nc; j += 32) {
+                                const uint64_t key = pk_key64(C[j], row0);
+                                const int rr = j + lower_bound_u64(Lst, nL, key);
+                                if (rr < k) out[rr] = key;
+                            }
+                            __syncwarp();
+                            const int nl = nL + nc < k ? nL + nc : k;
+                            uint64_t t_new = nl == k ? out[k - 1] : KEY_NONE;
+                            if (lane == 0) {
+                                const uint32_t T = ub[q];
+                                if (T != 0xFFFFFFFFu) t_new = min(t_new, (uint64_t)(2u * T + 1u) << 32);
+                                cur[q] = c0 ^ 1;
+                                len[q] = nl;
+                                cnt[q] = 0;
+                                uint64_t tq = min(tau[q], t_new);
+                                if (t_new != KEY_NONE) {
+                                    const unsigned long long old = atomicMin(
+                                        reinterpret_cast<unsigned long long*>(&a.tau_global[q]),
+                                        (unsigned long long)t_new);
+                                    tq = min(tq, (uint64_t)old);
+                                } else {
+                                    tq = min(tq, *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
+                                }
+                                tau[q] = tq;
+                                if (q < a.nqg) thr_s[q] = pk_thr(tq, x);
+                            }
+                            __syncwarp();
+                        }
+                    }
+                }
+                named_barrier(2, PK_EPI_THREADS);
+                if (ab) {
+                    bad = true;
+                    break;
+                }
+                my_need = false;
+            }
+            if (fin) break;
+        }
+        if (!bad && r < QN) {
+            int32_t* m = a.meta + ((int64_t)r * nslices + slice) * 2;
+            m[0] = len[r];
+            m[1] = cur[r];
+        }
+        __syncwarp();
+        if (warp == PK_EPI_WARP0 && lane == 0) *reinterpret_cast<volatile int*>(epi_done) = 1;
+    } else if (warp == PK_HELPER_WARP) {
+        // ---------------- union-bound helper ----------------
+        // For each query, the smallest T with count(Delta/2 <= T) >= k over
+        // the keys all slices have appended (real rows, so no row with a
+        // larger Delta/2 can be among the k nearest), scanning the workspace
+        // histogram from the smallest appended value up to the previous T.
+        while (!*reinterpret_cast<volatile int*>(epi_done) &&
+               !*reinterpret_cast<volatile int*>(abort_flag)) {
+            for (int q = 0; q < a.nqg; ++q) {
+                const uint32_t lo = __ldcg(&a.minhalf[q]);
+                const uint32_t prev = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
+                const uint32_t hi = min(prev, (uint32_t)(a.hist_bins - 1));
+                if (lo > hi) continue;
+                const uint32_t* H = a.hist + (int64_t)q * a.hist_bins;
+                uint32_t before = 0, T = 0xFFFFFFFFu;
+                for (uint32_t h0 = lo; h0 <= hi && T == 0xFFFFFFFFu; h0 += 32) {
+                    const uint32_t hb = h0 + (uint32_t)lane;
+                    const uint32_t c = hb <= hi ? __ldcg(&H[hb]) : 0u;
+                    uint32_t sum = c;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t nb = __shfl_up_sync(0xffffffffu, sum, o);
+                        if (lane >= o) sum += nb;
+                    }
+                    const uint32_t hit =
+                        __ballot_sync(0xffffffffu, c > 0 && before + sum >= (uint32_t)k);
+                    if (hit) T = h0 + (uint32_t)(__ffs(hit) - 1);
+                    before += __shfl_sync(0xffffffffu, sum, 31);
+                }
+                if (lane == 0 && T < prev) *reinterpret_cast<volatile uint32_t*>(&ub[q]) = T;
+                __syncwarp();
+            }
+            __nanosleep(2000);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (*(volatile int*)abort_flag && tid == 0) {
+        // after an abort, MMAs already issued may still be running: give
+        // them time to finish before TMEM is released
+        const uint64_t t0 = globaltimer_ns();
+        while (globaltimer_ns() - t0 < 5000000ull) __nanosleep(10000);
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == PK_MMA_WARP)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                     "r"(PK_TMEM_COLS)
+                     : "memory");
+}
+
+// Per pass: thresholds, histograms and minima of the union bound start empty.
+__global__ void pk_init_kernel(uint64_t* tau_global, uint32_t* hist, int hist_words,
+                               uint32_t* minhalf) {
+    if (threadIdx.x < PK_QN_MAX) {
+        tau_global[threadIdx.x] = KEY_NONE;
+        minhalf[threadIdx.x] = 0xFFFFFFFFu;
+    }
+    for (int i = threadIdx.x; i < hist_words; i += blockDim.x) hist[i] = 0u;
+}
+
+int pk_stages(int W, int qn) {
+    for (int s = PK_MAX_STAGES; s >= PK_MIN_STAGES; --s)
+        if (pk_layout(W, s, qn).total <= (size_t)PK_SMEM_LIMIT) return s;
+    return 0;
+}
+
+template <int QN>
+cudaError_t launch_pk(const CUtensorMap& tmap, const PkArgs& a, int nslices, cudaStream_t stream) {
+    const size_t smem = pk_layout(a.W, a.stages, QN).total;
+    cudaError_t e = cudaFuncSetAttribute(scan_mma_packed_kernel<QN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    TimedLaunch timer("scan_mma_packed", stream);
+    scan_mma_packed_kernel<QN><<<nslices, PK_THREADS, smem, stream>>>(tmap, a);
+    return cudaGetLastError();
+}
+
+struct PkPlan {
+    int nslices;
+    int64_t tiles_per_slice, ntiles;
+    size_t list_bytes, meta_bytes, hist_bytes, tau_bytes, ws_bytes;
+};
+
+PkPlan plan_pk(int64_t ns, int d, int k) {
+    PkPlan p{};
+    p.ntiles = std::max<int64_t>(1, (ns + PK_ROWS - 1) / PK_ROWS);
+    int64_t tps = (p.ntiles + num_sms() - 1) / num_sms();
+    tps = std::min(tps, PK_MAX_TILES_PER_SLICE);
+    p.tiles_per_slice = tps;
+    p.nslices = (int)((p.ntiles + tps - 1) / tps);
+    p.list_bytes = pk_align((size_t)PK_QN_MAX * p.nslices * 2 * k * 8, 256);
+    p.meta_bytes = pk_align((size_t)PK_QN_MAX * p.nslices * 2 * 4, 256);
+    p.hist_bytes = pk_align((size_t)PK_QN_MAX * (2 * d + 1) * 4, 256) + 256;  // + minima
+    p.tau_bytes = pk_align((size_t)PK_QN_MAX * 8, 256);
+    p.ws_bytes = p.list_bytes + p.meta_bytes + p.hist_bytes + p.tau_bytes;
+    return p;
+}
+
+}  // namespace
+
+bool mma_packed_supported(int64_t ns, int d, int k) {
+    const int W = (d + 63) / 64;
+    if (W % 2 != 0 || W > PK_W_MAX || k > MMA_K_MAX) return false;
+    return plan_pk(ns, d, k).nslices <= PK_MAX_SLICES;
+}
+
+size_t mma_packed_workspace(int64_t ns, int d, int k) { return plan_pk(ns, d, k).ws_bytes; }
+
+int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
+                           int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
+                           int32_t* status, cudaStream_t stream) {
+    if (!mma_packed_supported(ns, d, k)) return EVP_ERR_UNSUPPORTED;
+    const int W = (d + 63) / 64;
+    const PkPlan p = plan_pk(ns, d, k);
+    if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
+
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return EVP_ERR_CUDA;
+    CUtensorMap tmap;
+    const int pitch = 2 * W + 2;
+    cuuint64_t gdim[2] = {(cuuint64_t)(2 * W), (cuuint64_t)ns};
+    cuuint64_t gstride[1] = {(cuuint64_t)(16 * W)};
+    cuuint32_t box[2] = {(cuuint32_t)pitch, (cuuint32_t)PK_ROWS};
+    cuuint32_t estride[2] = {1, 1};
+    if (enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<uint64_t*>(S), gdim, gstride,
+            box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return EVP_ERR_CUDA;
+
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    PkArgs a{};
+    a.ns = ns;
+    a.W = W;
+    a.x = x;
+    a.k = k;
+    a.pitch = pitch;
+    a.ntiles = p.ntiles;
+    a.tiles_per_slice = p.tiles_per_slice;
+    a.lists = reinterpret_cast<uint64_t*>(w);
+    a.meta = reinterpret_cast<int32_t*>(w + p.list_bytes);
+    a.hist = reinterpret_cast<uint32_t*>(w + p.list_bytes + p.meta_bytes);
+    a.minhalf = reinterpret_cast<uint32_t*>(w + p.list_bytes + p.meta_bytes + p.hist_bytes - 256);
+    a.tau_global = reinterpret_cast<uint64_t*>(w + p.list_bytes + p.meta_bytes + p.hist_bytes);
+    a.hist_bins = 2 * x + 1;
+    a.status = status;
+
+    for (int64_t q0 = 0; q0 < nq; q0 += PK_QN_MAX) {
+        const int nqg = (int)std::min<int64_t>(PK_QN_MAX, nq - q0);
+        const int qn = nqg <= 16 ? 16 : nqg <= 32 ? 32 : 64;
+        a.Q = Q + q0 * 2 * W;
+        a.nqg = nqg;
+        a.stages = pk_stages(W, qn);
+        if (a.stages == 0) return EVP_ERR_UNSUPPORTED;
+        {
+            TimedLaunch timer("scan_init", stream);
+            pk_init_kernel<<<1, 256, 0, stream>>>(a.tau_global, a.hist, PK_QN_MAX * a.hist_bins,
+                                                  a.minhalf);
+        }
+        cudaError_t e;
+        if (qn == 16) e = launch_pk<16>(tmap, a, p.nslices, stream);
+        else if (qn == 32) e = launch_pk<32>(tmap, a, p.nslices, stream);
+        else e = launch_pk<64>(tmap, a, p.nslices, stream);
+        if (e != cudaSuccess) return EVP_ERR_CUDA;
+        const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, a.hist, a.minhalf,
+                                              a.hist_bins, nqg, p.nslices, k, ids + q0 * k,
+                                              dist + q0 * k, stream);
+        if (rc != EVP_OK) return rc;
+    }
+    return EVP_OK;
+}
+
+}  // namespace evp

@@ -102,16 +102,6 @@ __host__ __device__ inline SmemLayout smem_layout(int W, int stages, int qb) {
     return L;
 }
 
-__device__ inline int next_pow2(int v) {
-    int p = 32;
-    while (p < v) p <<= 1;
-    return p;
-}
-
-__device__ __forceinline__ void named_barrier(int id, int nthreads) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
-}
-
 // Ascending bitonic sort of buf[0, P) (P a power of two) by a team of TT
 // threads (t = thread index in the team) that synchronises with `sync`.
 template <typename Sync>
@@ -151,48 +141,6 @@ __device__ __forceinline__ int team_merge_topk(const uint64_t* L, int nL, const 
     }
     const int total = nL + nc;
     return total < k ? total : k;
-}
-
-// The smallest bin T with sum(hist[0..T]) >= k, scanning up from the
-// smallest non-empty bin; 0xFFFFFFFF if fewer than k keys are counted.
-// Team-wide (every thread gets the result); `scratch` holds TT/32 + 2 words.
-template <typename Sync>
-__device__ __forceinline__ uint32_t team_kth_bin(const uint32_t* hist, const uint32_t* minhalf,
-                                                 int bins, uint32_t k, uint32_t* scratch, int t,
-                                                 int TT, Sync& sync) {
-    const int nw = TT / 32, wt = t >> 5, ln = t & 31;
-    if (t == 0) {
-        scratch[nw] = __ldcg(minhalf);
-        scratch[nw + 1] = 0xFFFFFFFFu;
-    }
-    sync();
-    const uint32_t lo = scratch[nw];
-    uint32_t before = 0, T = 0xFFFFFFFFu;
-    for (uint32_t h0 = lo; h0 < (uint32_t)bins; h0 += (uint32_t)TT) {
-        const uint32_t h = h0 + (uint32_t)t;
-        const uint32_t c = h < (uint32_t)bins ? __ldcg(&hist[h]) : 0u;
-        uint32_t sum = c;  // inclusive scan over the warp
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t n = __shfl_up_sync(0xffffffffu, sum, o);
-            if (ln >= o) sum += n;
-        }
-        if (ln == 31) scratch[wt] = sum;
-        sync();
-        uint32_t off = 0, total = 0;
-        for (int w = 0; w < nw; ++w) {
-            const uint32_t v = scratch[w];
-            if (w < wt) off += v;
-            total += v;
-        }
-        sum += off;
-        if (c > 0 && before + sum >= k && before + sum - c < k) scratch[nw + 1] = h;
-        sync();
-        T = scratch[nw + 1];
-        before += total;
-        if (T != 0xFFFFFFFFu || before >= k) break;
-    }
-    return T;
 }
 
 // TPR threads share a row (each takes QB / TPR of the pass's queries), so a

@@ -27,7 +27,7 @@ EVP_ERR_CUDA = 5
 EVP_ERR_UNSUPPORTED = 6
 EVP_ERR_RANGE = 7
 
-PATH_AUTO, PATH_POPC, PATH_MMA = 0, 1, 2
+PATH_AUTO, PATH_POPC, PATH_MMA, PATH_MMA_PACKED = 0, 1, 2, 3
 MMA_MAX_K = 1024
 
 MAX_D_ENCODE = 2048

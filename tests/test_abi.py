@@ -107,7 +107,7 @@ def test_workspace_serves_every_smaller_batch(lib, d, ns):
     f = lib.ternary_knn_path_workspace
     f.restype = ctypes.c_size_t
     f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
-    for path in (0, 1, 2):
+    for path in (0, 1, 2, 3):
         for k in (1, 5, 20, 100, 200, 1000):
             if k > ns:
                 continue

@@ -22,7 +22,7 @@ def small_db(dev, evp_lib):
 
 
 @pytest.mark.parametrize("tensor_copy", [True, False])
-@pytest.mark.parametrize("path", [0, 1, 2])
+@pytest.mark.parametrize("path", [0, 1, 2, 3])
 def test_db_knn_matches_oracle(evp_lib, dev, small_db, tensor_copy, path):
     d, x, U, Qf, Ud, T = small_db
     db = evp_lib.Database(T, Ud, d, x, tensor_copy=tensor_copy)

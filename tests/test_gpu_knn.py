@@ -9,16 +9,28 @@ from paper_2506_00528_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-PATHS = [1, 2]   # EVP_PATH_POPC, EVP_PATH_MMA
+PATHS = [1, 2, 3]   # EVP_PATH_POPC, EVP_PATH_MMA, EVP_PATH_MMA_PACKED
+
+
+def packed_supported(d, k):
+    """Shapes the packed tensor-core path takes: d <= 768 with an even number
+    of 64-bit words per bitplane, k <= 1024."""
+    W = (d + 63) // 64
+    return W % 2 == 0 and W <= 12 and k <= 1024
 
 
 def _run(evp, Tq, Ts, d, x, k, dev, path=0):
-    if path == 2 and k > 1024:
-        pytest.skip("tensor-core path takes k <= 1024")
+    if path in (2, 3) and k > 1024:
+        pytest.skip("tensor-core paths take k <= 1024")
+    Qd = torch.from_numpy(Tq.view(np.int64)).to(dev)
+    Sd = torch.from_numpy(Ts.view(np.int64)).to(dev)
+    if path == 3 and not packed_supported(d, k):
+        with pytest.raises(evp.EvpError) as e:
+            evp.ternary_knn(Qd, Sd, d, x, k, path=path)
+        assert e.value.code == evp.EVP_ERR_UNSUPPORTED
+        pytest.skip("outside the packed path's shapes (refused as checked)")
     st = evp.new_status(dev)
-    ids, dist = evp.ternary_knn(torch.from_numpy(Tq.view(np.int64)).to(dev),
-                                torch.from_numpy(Ts.view(np.int64)).to(dev), d, x, k, status=st,
-                                path=path)
+    ids, dist = evp.ternary_knn(Qd, Sd, d, x, k, status=st, path=path)
     torch.cuda.synchronize()
     assert int(st.item()) == 0
     return ids.cpu().numpy(), dist.cpu().numpy()
@@ -87,7 +99,8 @@ def test_query_counts_span_passes(evp_lib, dev, nq, path):
     np.testing.assert_array_equal(ids, oi)
 
 
-@pytest.mark.parametrize("path,k", [(1, 300), (2, 128), (1, 1024), (2, 300), (2, 1024)])
+@pytest.mark.parametrize("path,k", [(1, 300), (2, 128), (1, 1024), (2, 300), (2, 1024),
+                                    (3, 128), (3, 300), (3, 1024)])
 def test_massive_ties(evp_lib, dev, path, k):
     """Only six distinct codes in the database: almost every Delta ties, so
     the (Delta, index) order decides everything, across slices and merges."""
@@ -102,9 +115,9 @@ def test_massive_ties(evp_lib, dev, path, k):
     np.testing.assert_array_equal(ids, oi)
 
 
-@pytest.mark.parametrize("path", PATHS)
-def test_identical_database(evp_lib, dev, path):
-    d, x = 64, 10
+@pytest.mark.parametrize("path,d", [(1, 64), (2, 64), (3, 128)])
+def test_identical_database(evp_lib, dev, path, d):
+    x = 10
     Vs = np.repeat(synth.ternary_random(1, d, x, stream=602), 9000, axis=0)
     Vq = synth.ternary_random(3, d, x, stream=603)
     ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, 64, dev, path)
@@ -113,11 +126,11 @@ def test_identical_database(evp_lib, dev, path):
     np.testing.assert_array_equal(dist, od)
 
 
-@pytest.mark.parametrize("path", PATHS)
-def test_descending_stream_worst_case(evp_lib, dev, path):
+@pytest.mark.parametrize("path,d", [(1, 64), (2, 64), (3, 128)])
+def test_descending_stream_worst_case(evp_lib, dev, path, d):
     """Rows ordered so that each is nearer than all earlier ones: every row
     enters the candidate buffers (the merge path under maximum pressure)."""
-    d, x, k = 64, 32, 100
+    x, k = 32, 100
     q = np.zeros((1, d), dtype=np.int8)
     q[0, :32] = 1
     rows = []
@@ -143,7 +156,9 @@ def test_argument_errors(evp_lib, dev):
     with pytest.raises(evp_lib.EvpError):
         evp_lib.ternary_knn(big[:1], big, 2048, 10, 3)         # d above the scan limit
     with pytest.raises(evp_lib.EvpError):
-        evp_lib.ternary_knn(Vs[:1], Vs, 64, 10, 9, path=3)     # unknown path
+        evp_lib.ternary_knn(Vs[:1], Vs, 64, 10, 9, path=4)     # unknown path
+    with pytest.raises(evp_lib.EvpError):
+        evp_lib.ternary_knn(Vs[:1], Vs, 64, 10, 9, path=3)     # packed path: odd word count
     many = torch.zeros((2000, 2), dtype=torch.int64, device=dev)
     with pytest.raises(evp_lib.EvpError):
         evp_lib.ternary_knn(many[:20], many, 64, 10, 1025, path=2)  # k above the limit
@@ -171,6 +186,28 @@ def test_tensor_path_cta_pair_and_single(evp_lib, dev, monkeypatch, pair, nq, ns
     Vs = synth.ternary_random(ns, d, x, stream=900 + d)
     Vq = synth.ternary_random(nq, d, x, stream=950 + d)
     ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path=2)
+    oi, od = oracle.knn(Vq, Vs, k)
+    np.testing.assert_array_equal(dist, od)
+    np.testing.assert_array_equal(ids, oi)
+
+
+@pytest.mark.parametrize("nq,ns,d,k", [(1, 3_001, 768, 10),     # one query: a 16-query pass
+                                       (16, 20_000, 768, 100),
+                                       (17, 20_000, 768, 100),  # 32-query pass
+                                       (64, 50_000, 768, 10),   # one full 64-query pass
+                                       (65, 50_000, 768, 10),   # a second pass of one query
+                                       (200, 9_000, 384, 50),   # four passes, d = 384
+                                       (5, 130_000, 128, 1024),
+                                       (33, 1_000, 256, 1000),
+                                       (40, 129, 640, 100)])    # one tile and a ragged row
+def test_packed_tensor_path(evp_lib, dev, nq, ns, d, k):
+    """The packed tensor-core scan (tiles unpacked on chip, database rows as
+    the MMA's M side) gives the oracle's ids and Delta bit for bit, across
+    pass sizes, K depths and ragged tiles."""
+    x = oracle.default_x(d)
+    Vs = synth.ternary_random(ns, d, x, stream=1100 + d)
+    Vq = synth.ternary_random(nq, d, x, stream=1150 + d)
+    ids, dist = _run(evp_lib, oracle.pack(Vq), oracle.pack(Vs), d, x, k, dev, path=3)
     oi, od = oracle.knn(Vq, Vs, k)
     np.testing.assert_array_equal(dist, od)
     np.testing.assert_array_equal(ids, oi)

@@ -31,7 +31,8 @@ def db_1m(dev):
     return U, Q, U.cpu().numpy(), Q.cpu().numpy()
 
 
-@pytest.mark.parametrize("x,path", [(64, 1), (256, 1), (384, 1), (256, 2), (64, 2)])
+@pytest.mark.parametrize("x,path", [(64, 1), (256, 1), (384, 1), (256, 2), (64, 2),
+                                    (64, 3), (256, 3), (384, 3)])
 def test_scale_1m_exhaustive_queries(evp_lib, dev, db_1m, x, path):
     U, Q, U_h, Q_h = db_1m
     d, k = 768, 100
