@@ -180,8 +180,9 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
  *   EVP_PATH_MMA_PACKED  tensor-core scan with the database as the 128-row
  *                  side: reads the packed codes once per 64 queries and
  *                  unpacks each tile on chip into tensor memory; needs
- *                  d <= 768 with ceil(d/64) even (else EVP_ERR_UNSUPPORTED)
- *                  and at most 2^20 * 1024 rows; best for medium batches.
+ *                  d <= 768 with ceil(d/64) even and k <= 256 (else
+ *                  EVP_ERR_UNSUPPORTED) and at most 2^20 * 256 rows; best
+ *                  for medium batches.
  *   EVP_PATH_AUTO  POPC for nq <= EVP_AUTO_POPC_MAX_NQ; MMA_PACKED (where
  *                  supported) up to EVP_AUTO_PACKED_MAX_NQ queries against a
  *                  resident database holding its e4m3 copy, and up to
@@ -198,7 +199,7 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
 #define EVP_PATH_MMA  2
 #define EVP_PATH_MMA_PACKED 3
 #define EVP_AUTO_POPC_MAX_NQ 3
-#define EVP_AUTO_PACKED_MAX_NQ 48
+#define EVP_AUTO_PACKED_MAX_NQ 64
 #define EVP_AUTO_PACKED_MAX_NQ_NO_COPY 128
 #define EVP_MMA_MAX_K 1024
 

@@ -19,8 +19,8 @@
 //     in which the non-zero bit of each dimension sits next to its sign bit.
 //
 // Kernel (one CTA per SM, persistent over a contiguous slice of 128-row
-// tiles, 480 threads in five roles that meet only at mbarriers):
-//   warp 13     TMA producer: tiles of packed rows (box 2W + 2 words wide,
+// tiles, 608 threads in five roles that meet only at mbarriers):
+//   warp 17     TMA producer: tiles of packed rows (box 2W + 2 words wide,
 //               the padding words read as 0 so that 16-byte row reads are
 //               bank-conflict free) through a ring of mbarrier stages;
 //   warps 0-7   unpack, two threads per database row (TMEM lane): each
@@ -28,20 +28,22 @@
 //               stage, releases the stage and writes the unpacked e4m3
 //               columns with tcgen05.st into one of two A buffers (192
 //               columns each) once the MMAs have read it;
-//   warp 12     allocates the 512 TMEM columns and issues the MMAs from one
+//   warp 16     allocates the 512 TMEM columns and issues the MMAs from one
 //               thread: A (the unpacked tile) from TMEM, B (the queries)
 //               from shared memory (SWIZZLE_128B, written once at start),
-//               D into one of two accumulators (QN columns each);
-//   warps 8-11  epilogue, one thread per row: reads the row's QN
-//               accumulator columns, and appends rows that beat a query's
-//               threshold to that query's candidate buffer in shared memory;
-//               the four warps merge full buffers (bitonic sort + merge
-//               path) into per-(query, slice) sorted lists of the k best in
-//               the workspace;
-//   warp 14     union-bound helper: per query, the k-th smallest Delta/2
-//               over every row any slice has appended, from a histogram in
-//               the workspace that all slices share; the epilogue folds it
-//               (and the other slices' list thresholds) into its own.
+//               D into one of two accumulators (QN columns each), one
+//               commit per tile;
+//   warps 8-15  epilogue, two threads per row (each half of the queries):
+//               each warp reads its rows' accumulator columns and appends
+//               rows that beat a query's threshold to candidate buffers of
+//               its own, which it merges (bitonic sort + merge path) into
+//               sorted lists of the k best of its own in the workspace (one
+//               list per query and row quadrant of the CTA), so epilogue
+//               warps never wait for one another;
+//   warp 18     union-bound helper: per query, the k-th smallest Delta/2
+//               over every row any list has taken, from a histogram in the
+//               workspace that all CTAs share; the epilogue warps fold it
+//               (and the other lists' thresholds) into their own.
 // The per-query final merge of the popcount path combines the lists.
 // Every mbarrier wait is bounded (2 s): on expiry the CTA reports
 // EVP_ERR_TIMEOUT, raises its abort flag (every other wait then gives up at
@@ -56,18 +58,19 @@ namespace {
 
 constexpr int PK_ROWS = 128;                         // database rows per tile = TMEM lanes
 constexpr int PK_UNPACK_WARPS = 8;                   // warps 0-7: two threads per row
-constexpr int PK_EPI_WARP0 = 8;                      // warps 8-11: one thread per row
-constexpr int PK_EPI_WARPS = 4;
-constexpr int PK_EPI_THREADS = PK_EPI_WARPS * 32;
-constexpr int PK_MMA_WARP = 12;
-constexpr int PK_TMA_WARP = 13;
-constexpr int PK_HELPER_WARP = 14;
-constexpr int PK_THREADS = 15 * 32;
+constexpr int PK_EPI_WARP0 = 8;                      // warps 8-15: two threads per row
+constexpr int PK_EPI_WARPS = 8;
+constexpr int PK_LISTS_PER_CTA = 4;                  // one slice list per row quadrant
+constexpr int PK_MMA_WARP = 16;
+constexpr int PK_TMA_WARP = 17;
+constexpr int PK_HELPER_WARP = 18;
+constexpr int PK_THREADS = 19 * 32;
 constexpr int PK_STAGE_LIST_K = 128;                 // merges stage the list in shared memory up to this k
+constexpr int PK_K_MAX = 256;                        // largest k of this path
 constexpr int PK_QN_MAX = 64;                        // queries per pass
 constexpr int PK_W_MAX = 12;                         // words per bitplane: d <= 768
-constexpr int PK_CAP = 256;                          // candidate slots per query
-constexpr int PK_MERGE_AT = PK_CAP - PK_ROWS;        // merge at this count: a tile adds <= PK_ROWS
+constexpr int PK_CAP = 64;                           // candidate slots per (epilogue warp, query)
+constexpr int PK_MERGE_AT = PK_CAP - 32;             // merge at this count: a tile adds <= 32
 constexpr int PK_LOCAL_BITS = 20;                    // row-in-slice bits of a candidate key
 constexpr int64_t PK_MAX_TILES_PER_SLICE = (int64_t(1) << PK_LOCAL_BITS) / PK_ROWS;
 constexpr int PK_MAX_STAGES = 6;
@@ -88,8 +91,8 @@ struct PkArgs {
     int pitch;             // uint64 words per staged row (2W + 2)
     int stages;
     int64_t tiles_per_slice, ntiles;
-    uint64_t* lists;       // [PK_QN_MAX][nslices][2][k]
-    int32_t* meta;         // [PK_QN_MAX][nslices][2]: (length, current buffer)
+    uint64_t* lists;       // [PK_QN_MAX][4 * CTAs][2][k]: one list per (query, CTA, row quadrant)
+    int32_t* meta;         // [PK_QN_MAX][4 * CTAs][2]: (length, current buffer)
     uint64_t* tau_global;  // [PK_QN_MAX]
     uint32_t* hist;        // [PK_QN_MAX][hist_bins]
     uint32_t* minhalf;     // [PK_QN_MAX]
@@ -104,19 +107,24 @@ struct PkLayout {
         misc_off, total;
 };
 
+// Per-(epilogue warp, query) state: warp e (0-7) serves the rows of
+// quadrant e % 4 against queries [(e / 4) qn/2, (e / 4 + 1) qn/2); its
+// entry j is at index e * qn/2 + j of each array.
+
 // Shared-memory carve-up (offsets from a 1024-byte aligned base; `total`
 // includes the alignment slack of the dynamic allocation).
 __host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn) {
     PkLayout L;
     L.stage_bytes = pk_align((size_t)PK_ROWS * (2 * W + 2) * 8, 1024);
     L.b_off = L.stage_bytes * stages;
+    const size_t states = (size_t)PK_EPI_WARPS * (qn / 2);
     L.cand_off = L.b_off + (size_t)(W / 2) * qn * 128;  // W/2 K-chunks of qn x 128 B
-    L.scratch_off = L.cand_off + (size_t)qn * PK_CAP * 4;  // one staged list per epilogue warp
+    L.scratch_off = L.cand_off + states * PK_CAP * 4;    // one staged list per epilogue warp
     L.tau_off = L.scratch_off + (size_t)PK_EPI_WARPS * PK_STAGE_LIST_K * 8;
-    L.thr_off = L.tau_off + (size_t)qn * 8;
-    L.ub_off = L.thr_off + (size_t)qn * 4;
+    L.thr_off = L.tau_off + states * 8;
+    L.ub_off = L.thr_off + states * 4;
     L.cnt_off = L.ub_off + (size_t)qn * 4;
-    L.bar_off = pk_align(L.cnt_off + (size_t)4 * qn * 4, 8);
+    L.bar_off = pk_align(L.cnt_off + 4 * states * 4, 8);
     L.misc_off = L.bar_off + (size_t)(2 * stages + 6) * 8;
     L.total = L.misc_off + 16 + 1024;
     return L;
@@ -191,21 +199,6 @@ __device__ __forceinline__ void tmem_ld_wait(uint32_t taddr, uint32_t (&v)[N]) {
             : "r"(taddr)
             : "memory");
     }
-}
-
-// Named barrier over `n` threads that also returns whether any of them
-// passed p = true.
-__device__ __forceinline__ bool bar_red_or(int id, int n, bool p) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred pi, po;\n\t"
-        "setp.ne.u32 pi, %3, 0;\n\t"
-        "bar.red.or.pred po, %1, %2, pi;\n\t"
-        "selp.u32 %0, 1, 0, po;\n\t}"
-        : "=r"(r)
-        : "r"(id), "r"(n), "r"((uint32_t)p)
-        : "memory");
-    return r != 0;
 }
 
 // TMEM columns of one 64-bit word pair of the bitplanes (64 dimensions per
@@ -289,15 +282,17 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
     const PkLayout L = pk_layout(W, S, QN);
     uint8_t* stages = smem;
     uint8_t* qop = smem + L.b_off;  // query operand, W/2 chunks of QN x 128 B
-    uint32_t* cand = reinterpret_cast<uint32_t*>(smem + L.cand_off);
+    constexpr int QH = QN / 2;  // queries per epilogue warp
+    constexpr int NSTATE = PK_EPI_WARPS * QH;
+    uint32_t* cand = reinterpret_cast<uint32_t*>(smem + L.cand_off);   // [NSTATE][PK_CAP]
     uint64_t* scratch = reinterpret_cast<uint64_t*>(smem + L.scratch_off);
-    uint64_t* tau = reinterpret_cast<uint64_t*>(smem + L.tau_off);
-    float* thr_s = reinterpret_cast<float*>(smem + L.thr_off);
-    uint32_t* ub = reinterpret_cast<uint32_t*>(smem + L.ub_off);
-    int* cnt = reinterpret_cast<int*>(smem + L.cnt_off);
-    int* len = cnt + QN;
-    int* cur = len + QN;
-    uint32_t* lmin = reinterpret_cast<uint32_t*>(cur + QN);
+    uint64_t* tau = reinterpret_cast<uint64_t*>(smem + L.tau_off);     // [NSTATE] thresholds
+    float* thr_s = reinterpret_cast<float*>(smem + L.thr_off);         // [NSTATE] on D
+    uint32_t* ub = reinterpret_cast<uint32_t*>(smem + L.ub_off);       // [QN] union bounds
+    int* cnt = reinterpret_cast<int*>(smem + L.cnt_off);               // [NSTATE] candidates
+    int* len = cnt + NSTATE;                                           // [NSTATE] list lengths
+    int* cur = len + NSTATE;                                           // [NSTATE] list buffers
+    uint32_t* lmin = reinterpret_cast<uint32_t*>(cur + NSTATE);        // [NSTATE] least Delta/2
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L.bar_off);
     uint64_t* full = bars;                 // [S]  TMA -> unpack warps
     uint64_t* empty = bars + S;            // [S]  unpack warps -> TMA
@@ -307,8 +302,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
     uint64_t* d_empty = bars + 2 * S + 4;  // [2]  epilogue -> MMA (accumulator read)
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
-    int* epi_bad = abort_flag + 1;         // an epilogue warp gave up on a wait
-    int* epi_done = abort_flag + 2;        // the epilogue finished (the helper stops)
+    int* epi_done = abort_flag + 1;        // epilogue warps finished (the helper stops at 8)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nslices = gridDim.x, slice = blockIdx.x;
@@ -331,7 +325,6 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             mbar_init(&d_empty[b], PK_EPI_WARPS);
         }
         *abort_flag = 0;
-        *epi_bad = 0;
         *epi_done = 0;
         fence_mbar_init();
     }
@@ -362,15 +355,16 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         }
         fence_proxy_async_smem();  // generic-proxy writes read by the tensor core
     }
-    if (tid < QN) {
-        tau[tid] = KEY_NONE;
-        thr_s[tid] = tid < a.nqg ? PK_ADMIT_ALL : INFINITY;  // padding queries never admit
-        ub[tid] = 0xFFFFFFFFu;
-        cnt[tid] = 0;
-        len[tid] = 0;
-        cur[tid] = 0;
-        lmin[tid] = 0xFFFFFFFFu;
+    for (int i = tid; i < NSTATE; i += PK_THREADS) {
+        const int q = (i / QH >> 2) * QH + i % QH;
+        tau[i] = KEY_NONE;
+        thr_s[i] = q < a.nqg ? PK_ADMIT_ALL : INFINITY;  // padding queries never admit
+        cnt[i] = 0;
+        len[i] = 0;
+        cur[i] = 0;
+        lmin[i] = 0xFFFFFFFFu;
     }
+    if (tid < QN) ub[tid] = 0xFFFFFFFFu;
     if (warp == PK_MMA_WARP) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
@@ -499,200 +493,185 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         }
     } else if (warp < PK_EPI_WARP0 + PK_EPI_WARPS) {
         // ---------------- epilogue warps ----------------
-        const int ew = warp - PK_EPI_WARP0;
-        const int r = ew * 32 + lane;  // row in the tile = TMEM lane (warp % 4 == ew)
-        const uint32_t lane_off = (uint32_t)(ew * 32) << 16;
-        bool bad = false;      // this warp gave up on a wait
-        bool my_need = false;  // a candidate buffer this thread appended to needs a merge
-        for (int t = 0;; ++t) {
-            const bool fin = t == ntl;
-            if (!fin && !bad) {
-                const int b = t & 1;
-                int got = 1;
-                if (lane == 0)
-                    got = mbar_wait_or_abort(&d_full[b], (uint32_t)((t >> 1) & 1), abort_flag);
-                got = __shfl_sync(0xffffffffu, got, 0);
-                if (!got) {
-                    bad = true;
-                    if (lane == 0) {
-                        *(volatile int*)epi_bad = 1;
-                        give_up();
-                    }
-                } else {
-                    tc_fence_after();
-                    const int64_t row = (tile0 + t) * PK_ROWS + r;
-                    const uint32_t dcol = tmem_base + lane_off + (uint32_t)(PK_D_COL0 + b * QN);
-                    // chunks of QC accumulator columns (queries), the accumulator
-                    // released after the last chunk is read
-                    constexpr int QC = QN < 32 ? QN : 32;
-#pragma unroll
-                    for (int ci = 0; ci < QN / QC; ++ci) {
-                        uint32_t v[QC];
-                        tmem_ld_wait<QC>(dcol + (uint32_t)(ci * QC), v);
-                        if (ci == QN / QC - 1) {
-                            tc_fence_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(&d_empty[b]);
-                        }
-                        // D - threshold per query, then the largest of them (the
-                        // thresholds are finite half-integers, -2^22 or +inf:
-                        // D - threshold is exact and D = (D - threshold) + threshold)
-                        const float4* th4 = reinterpret_cast<const float4*>(thr_s + ci * QC);
-                        float gap = -INFINITY;
-#pragma unroll
-                        for (int c = 0; c < QC / 4; ++c) {
-                            const float4 th = th4[c];
-                            const float g0 = __uint_as_float(v[4 * c]) - th.x;
-                            const float g1 = __uint_as_float(v[4 * c + 1]) - th.y;
-                            const float g2 = __uint_as_float(v[4 * c + 2]) - th.z;
-                            const float g3 = __uint_as_float(v[4 * c + 3]) - th.w;
-                            v[4 * c] = __float_as_uint(g0);
-                            v[4 * c + 1] = __float_as_uint(g1);
-                            v[4 * c + 2] = __float_as_uint(g2);
-                            v[4 * c + 3] = __float_as_uint(g3);
-                            gap = fmaxf(gap, fmaxf(fmaxf(g0, g1), fmaxf(g2, g3)));
-                        }
-                        const bool live = gap > 0.f && row < a.ns;
-                        if (!__any_sync(0xffffffffu, live)) continue;
-                        uint32_t msk = 0;
-#pragma unroll
-                        for (int q = 0; q < QC; ++q)
-                            msk |= (live && __uint_as_float(v[q]) > 0.f ? 1u : 0u) << q;
-                        const uint32_t any = __reduce_or_sync(0xffffffffu, msk);
-#pragma unroll
-                        for (int qq = 0; qq < QC; ++qq) {
-                            if (!((any >> qq) & 1u)) continue;
-                            const int q = ci * QC + qq;
-                            // Delta = 2x - D lies in [0, 4x] for codes with x non-zeros;
-                            // clamped so that other codes cannot index outside the histogram
-                            const float dq = __uint_as_float(v[qq]) + thr_s[q];
-                            const uint32_t delta = (uint32_t)min(
-                                max(2 * x - __float2int_rn(dq), 0), 4 * x);
-                            bool c = (msk >> qq) & 1u;
-                            if (c) c = (((uint64_t)delta << 32) | (uint64_t)row) < tau[q];
-                            const uint32_t am = __ballot_sync(0xffffffffu, c);
-                            if (!am) continue;
-                            const int leader = __ffs(am) - 1;
-                            int pos0 = 0;
-                            if (lane == leader) pos0 = atomicAdd(&cnt[q], __popc(am));
-                            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
-                            const uint32_t half = delta >> 1;
-                            if (c) {
-                                const int rank = __popc(am & ((1u << lane) - 1u));
-                                cand[q * PK_CAP + pos0 + rank] =
-                                    (half << PK_LOCAL_BITS) | (uint32_t)(row - row0);
-                                // each row is appended at most once: count it for the union bound
-                                atomicAdd(&a.hist[(int64_t)q * a.hist_bins + half], 1u);
-                            }
-                            const uint32_t wmin = __reduce_min_sync(0xffffffffu, c ? half : 0xFFFFFFFFu);
-                            if (lane == leader) {
-                                if (wmin < lmin[q]) {
-                                    atomicMin(&lmin[q], wmin);
-                                    atomicMin(&a.minhalf[q], wmin);
-                                }
-                                if (pos0 + __popc(am) >= PK_MERGE_AT) my_need = true;
-                            }
-                        }
-                    }
-                }
-            }
-            // One barrier per tile; merges, threshold folds, the end and an
-            // abort take a second phase that every epilogue thread enters.
+        // Warp e serves rows of quadrant e % 4 (its TMEM lanes) against
+        // queries (e / 4) QH + j, j < QH, with candidate buffers, slice lists
+        // and thresholds of its own: no epilogue warp waits for another.
+        const int e = warp - PK_EPI_WARP0;
+        const int quad = e & 3, qbase = (e >> 2) * QH;
+        const int r = quad * 32 + lane;  // row in the tile = TMEM lane
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const int lslice = slice * PK_LISTS_PER_CTA + quad;  // this warp's list index
+        const int nlists = nslices * PK_LISTS_PER_CTA;
+        uint32_t* candw = cand + e * QH * PK_CAP;
+        uint64_t* tauw = tau + e * QH;
+        float* thrw = thr_s + e * QH;
+        int* cntw = cnt + e * QH;
+        int* lenw = len + e * QH;
+        int* curw = cur + e * QH;
+        uint32_t* lminw = lmin + e * QH;
+        // candidates of entry j -> the (query, slice) list: sort, merge path,
+        // new threshold from the list's k-th key and the union bound
+        auto merge = [&](int j, bool fin) {
+            const int q = qbase + j, nc = cntw[j];
+            uint32_t* C = candw + j * PK_CAP;
+            const int P = next_pow2(nc);
+            for (int i = nc + lane; i < P; i += 32) C[i] = 0xFFFFFFFFu;
             __syncwarp();
-            const bool phase = bar_red_or(1, PK_EPI_THREADS, my_need || bad);
-            const bool fold = (t & 7) == 7;
-            if (phase || fin || fold) {
-                const bool ab = *(volatile int*)epi_bad != 0;
-                if (!ab) {
-                    if (fold) {
-                        // other slices' thresholds and the union bound, one query per lane
-                        for (int q = ew + PK_EPI_WARPS * lane; q < a.nqg; q += PK_EPI_THREADS) {
-                            uint64_t tq = min(tau[q],
-                                              *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
-                            const uint32_t T = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
-                            if (T != 0xFFFFFFFFu) tq = min(tq, (uint64_t)(2u * T + 1u) << 32);
-                            tau[q] = tq;
-                            thr_s[q] = pk_thr(tq, x);
-                        }
-                        __syncwarp();
-                    }
-                    for (int q = ew; q < QN; q += PK_EPI_WARPS) {
-                        const int nc = cnt[q];
-                        if (nc >= PK_MERGE_AT || (fin && nc > 0)) {
-                            uint32_t* C = cand + q * PK_CAP;
-                            const int P = next_pow2(nc);
-                            for (int i = nc + lane; i < P; i += 32) C[i] = 0xFFFFFFFFu;
-                            __syncwarp();
-                            warp_sort_u32(C, P, lane);
-                            uint64_t* base = a.lists + ((int64_t)q * nslices + slice) * 2 * k;
-                            const int c0 = cur[q], nL = len[q];
-                            const uint64_t* Lst = base + (int64_t)c0 * k;
-                            uint64_t* out = base + (int64_t)(c0 ^ 1) * k;
-                            if (k <= PK_STAGE_LIST_K) {
-                                // the list, read once, is searched in shared memory
-                                uint64_t* Ls = scratch + ew * PK_STAGE_LIST_K;
-                                for (int i = lane; i < nL; i += 32) Ls[i] = Lst[i];
-                                __syncwarp();
-                                Lst = Ls;
-                            }
-                            for (int i = lane; i < nL; i += 32) {
-                                const uint64_t key = Lst[i];
-                                const int rr = i + lower_bound_cand(C, nc, key, row0);
-                                if (rr < k) out[rr] = key;
-                            }
-                            for (int j = lane; j < nc; j += 32) {
-                                const uint64_t key = pk_key64(C[j], row0);
-                                const int rr = j + lower_bound_u64(Lst, nL, key);
-                                if (rr < k) out[rr] = key;
-                            }
-                            __syncwarp();
-                            const int nl = nL + nc < k ? nL + nc : k;
-                            uint64_t t_new = nl == k ? out[k - 1] : KEY_NONE;
-                            if (lane == 0) {
-                                const uint32_t T = ub[q];
-                                if (T != 0xFFFFFFFFu) t_new = min(t_new, (uint64_t)(2u * T + 1u) << 32);
-                                cur[q] = c0 ^ 1;
-                                len[q] = nl;
-                                cnt[q] = 0;
-                                uint64_t tq = min(tau[q], t_new);
-                                if (t_new != KEY_NONE) {
-                                    const unsigned long long old = atomicMin(
-                                        reinterpret_cast<unsigned long long*>(&a.tau_global[q]),
-                                        (unsigned long long)t_new);
-                                    tq = min(tq, (uint64_t)old);
-                                } else {
-                                    tq = min(tq, *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
-                                }
-                                tau[q] = tq;
-                                if (q < a.nqg) thr_s[q] = pk_thr(tq, x);
-                            }
-                            __syncwarp();
-                        }
-                    }
-                }
-                named_barrier(2, PK_EPI_THREADS);
-                if (ab) {
-                    bad = true;
-                    break;
-                }
-                my_need = false;
+            warp_sort_u32(C, P, lane);
+            uint64_t* base = a.lists + ((int64_t)q * nlists + lslice) * 2 * k;
+            const int c0 = curw[j], nL = lenw[j];
+            const uint64_t* Lst = base + (int64_t)c0 * k;
+            uint64_t* out = base + (int64_t)(c0 ^ 1) * k;
+            if (k <= PK_STAGE_LIST_K) {
+                // the list, read once, is searched in shared memory
+                uint64_t* Ls = scratch + e * PK_STAGE_LIST_K;
+                for (int i = lane; i < nL; i += 32) Ls[i] = Lst[i];
+                __syncwarp();
+                Lst = Ls;
             }
-            if (fin) break;
+            for (int i = lane; i < nL; i += 32) {
+                const uint64_t key = Lst[i];
+                const int rr = i + lower_bound_cand(C, nc, key, row0);
+                if (rr < k) out[rr] = key;
+            }
+            for (int i = lane; i < nc; i += 32) {
+                const uint64_t key = pk_key64(C[i], row0);
+                const int rr = i + lower_bound_u64(Lst, nL, key);
+                if (rr < k) out[rr] = key;
+            }
+            __syncwarp();
+            const int nl = nL + nc < k ? nL + nc : k;
+            if (lane == 0) {
+                uint64_t t_new = nl == k ? out[k - 1] : KEY_NONE;
+                const uint32_t T = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
+                if (!fin && T != 0xFFFFFFFFu) t_new = min(t_new, (uint64_t)(2u * T + 1u) << 32);
+                curw[j] = c0 ^ 1;
+                lenw[j] = nl;
+                cntw[j] = 0;
+                uint64_t tq = min(tauw[j], t_new);
+                if (t_new != KEY_NONE) {
+                    const unsigned long long old =
+                        atomicMin(reinterpret_cast<unsigned long long*>(&a.tau_global[q]),
+                                  (unsigned long long)t_new);
+                    tq = min(tq, (uint64_t)old);
+                }
+                tauw[j] = tq;
+                if (q < a.nqg) thrw[j] = pk_thr(tq, x);
+            }
+            __syncwarp();
+        };
+        bool ok = true;
+        for (int t = 0; t < ntl; ++t) {
+            const int b = t & 1;
+            int got = 1;
+            if (lane == 0) got = mbar_wait_or_abort(&d_full[b], (uint32_t)((t >> 1) & 1), abort_flag);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) {
+                if (lane == 0) give_up();
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            uint32_t v[QH];
+            tmem_ld_wait<QH>(tmem_base + lane_off + (uint32_t)(PK_D_COL0 + b * QN + qbase), v);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&d_empty[b]);
+            const int64_t row = (tile0 + t) * PK_ROWS + r;
+            // D - threshold per query, then the largest of them (thresholds
+            // are finite half-integers, -2^22 or +inf: D - threshold is
+            // exact and D = (D - threshold) + threshold)
+            const float4* th4 = reinterpret_cast<const float4*>(thrw);
+            float gap = -INFINITY;
+#pragma unroll
+            for (int c = 0; c < QH / 4; ++c) {
+                const float4 th = th4[c];
+                const float g0 = __uint_as_float(v[4 * c]) - th.x;
+                const float g1 = __uint_as_float(v[4 * c + 1]) - th.y;
+                const float g2 = __uint_as_float(v[4 * c + 2]) - th.z;
+                const float g3 = __uint_as_float(v[4 * c + 3]) - th.w;
+                v[4 * c] = __float_as_uint(g0);
+                v[4 * c + 1] = __float_as_uint(g1);
+                v[4 * c + 2] = __float_as_uint(g2);
+                v[4 * c + 3] = __float_as_uint(g3);
+                gap = fmaxf(gap, fmaxf(fmaxf(g0, g1), fmaxf(g2, g3)));
+            }
+            const bool live = gap > 0.f && row < a.ns;
+            if (__any_sync(0xffffffffu, live)) {
+                uint32_t msk = 0;
+#pragma unroll
+                for (int j = 0; j < QH; ++j)
+                    msk |= (live && __uint_as_float(v[j]) > 0.f ? 1u : 0u) << j;
+                const uint32_t any = __reduce_or_sync(0xffffffffu, msk);
+                bool need = false;
+#pragma unroll
+                for (int j = 0; j < QH; ++j) {
+                    if (!((any >> j) & 1u)) continue;
+                    const int q = qbase + j;
+                    // Delta = 2x - D lies in [0, 4x] for codes with x non-zeros;
+                    // clamped so that other codes cannot index outside the histogram
+                    const float dq = __uint_as_float(v[j]) + thrw[j];
+                    const uint32_t delta = (uint32_t)min(max(2 * x - __float2int_rn(dq), 0), 4 * x);
+                    bool c = (msk >> j) & 1u;
+                    if (c) c = (((uint64_t)delta << 32) | (uint64_t)row) < tauw[j];
+                    const uint32_t am = __ballot_sync(0xffffffffu, c);
+                    if (!am) continue;
+                    const int pos0 = cntw[j];
+                    const uint32_t half = delta >> 1;
+                    if (c) {
+                        const int rank = __popc(am & ((1u << lane) - 1u));
+                        candw[j * PK_CAP + pos0 + rank] = (half << PK_LOCAL_BITS) | (uint32_t)(row - row0);
+                        // each row is appended at most once: count it for the union bound
+                        atomicAdd(&a.hist[(int64_t)q * a.hist_bins + half], 1u);
+                    }
+                    const uint32_t wmin = __reduce_min_sync(0xffffffffu, c ? half : 0xFFFFFFFFu);
+                    __syncwarp();
+                    if (lane == 0) {
+                        cntw[j] = pos0 + __popc(am);
+                        if (wmin < lminw[j]) {
+                            lminw[j] = wmin;
+                            atomicMin(&a.minhalf[q], wmin);
+                        }
+                    }
+                    need |= pos0 + __popc(am) >= PK_MERGE_AT;
+                    __syncwarp();
+                }
+                if (need) {
+                    for (int j = 0; j < QH; ++j)
+                        if (cntw[j] >= PK_MERGE_AT) merge(j, false);
+                }
+            }
+            if ((t & 7) == 7) {
+                // other slices' thresholds and the union bound, one query per lane
+                if (lane < QH && qbase + lane < a.nqg) {
+                    const int q = qbase + lane;
+                    uint64_t tq = min(tauw[lane], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
+                    const uint32_t T = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
+                    if (T != 0xFFFFFFFFu) tq = min(tq, (uint64_t)(2u * T + 1u) << 32);
+                    tauw[lane] = tq;
+                    thrw[lane] = pk_thr(tq, x);
+                }
+                __syncwarp();
+            }
         }
-        if (!bad && r < QN) {
-            int32_t* m = a.meta + ((int64_t)r * nslices + slice) * 2;
-            m[0] = len[r];
-            m[1] = cur[r];
+        if (ok) {
+            for (int j = 0; j < QH; ++j)
+                if (cntw[j] > 0) merge(j, true);
+            if (lane < QH) {
+                int32_t* m = a.meta + ((int64_t)(qbase + lane) * nlists + lslice) * 2;
+                m[0] = lenw[lane];
+                m[1] = curw[lane];
+            }
         }
         __syncwarp();
-        if (warp == PK_EPI_WARP0 && lane == 0) *reinterpret_cast<volatile int*>(epi_done) = 1;
+        if (lane == 0) atomicAdd(epi_done, 1);
     } else if (warp == PK_HELPER_WARP) {
         // ---------------- union-bound helper ----------------
         // For each query, the smallest T with count(Delta/2 <= T) >= k over
         // the keys all slices have appended (real rows, so no row with a
         // larger Delta/2 can be among the k nearest), scanning the workspace
         // histogram from the smallest appended value up to the previous T.
-        while (!*reinterpret_cast<volatile int*>(epi_done) &&
+        while (*reinterpret_cast<volatile int*>(epi_done) < PK_EPI_WARPS &&
                !*reinterpret_cast<volatile int*>(abort_flag)) {
             for (int q = 0; q < a.nqg; ++q) {
                 const uint32_t lo = __ldcg(&a.minhalf[q]);
@@ -700,19 +679,35 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                 const uint32_t hi = min(prev, (uint32_t)(a.hist_bins - 1));
                 if (lo > hi) continue;
                 const uint32_t* H = a.hist + (int64_t)q * a.hist_bins;
+                // 8 consecutive bins per lane, 256 per round trip to L2
                 uint32_t before = 0, T = 0xFFFFFFFFu;
-                for (uint32_t h0 = lo; h0 <= hi && T == 0xFFFFFFFFu; h0 += 32) {
-                    const uint32_t hb = h0 + (uint32_t)lane;
-                    const uint32_t c = hb <= hi ? __ldcg(&H[hb]) : 0u;
-                    uint32_t sum = c;
+                for (uint32_t h0 = lo; h0 <= hi && T == 0xFFFFFFFFu; h0 += 256) {
+                    const uint32_t hb = h0 + 8u * (uint32_t)lane;
+                    uint32_t c8[8], own = 0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        c8[u] = hb + u <= hi ? __ldcg(&H[hb + u]) : 0u;
+                        own += c8[u];
+                    }
+                    uint32_t sum = own;  // inclusive scan of the lanes' sums
 #pragma unroll
                     for (int o = 1; o < 32; o <<= 1) {
                         const uint32_t nb = __shfl_up_sync(0xffffffffu, sum, o);
                         if (lane >= o) sum += nb;
                     }
-                    const uint32_t hit =
-                        __ballot_sync(0xffffffffu, c > 0 && before + sum >= (uint32_t)k);
-                    if (hit) T = h0 + (uint32_t)(__ffs(hit) - 1);
+                    const uint32_t hit = __ballot_sync(0xffffffffu, before + sum >= (uint32_t)k);
+                    if (hit) {
+                        const int l0 = __ffs(hit) - 1;
+                        if (lane == l0) {
+                            uint32_t cum = before + sum - own;
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                cum += c8[u];
+                                if (cum >= (uint32_t)k && T == 0xFFFFFFFFu) T = hb + u;
+                            }
+                        }
+                        T = __shfl_sync(0xffffffffu, T, l0);
+                    }
                     before += __shfl_sync(0xffffffffu, sum, 31);
                 }
                 if (lane == 0 && T < prev) *reinterpret_cast<volatile uint32_t*>(&ub[q]) = T;
@@ -778,8 +773,9 @@ PkPlan plan_pk(int64_t ns, int d, int k) {
     tps = std::min(tps, PK_MAX_TILES_PER_SLICE);
     p.tiles_per_slice = tps;
     p.nslices = (int)((p.ntiles + tps - 1) / tps);
-    p.list_bytes = pk_align((size_t)PK_QN_MAX * p.nslices * 2 * k * 8, 256);
-    p.meta_bytes = pk_align((size_t)PK_QN_MAX * p.nslices * 2 * 4, 256);
+    const size_t lists = (size_t)PK_QN_MAX * p.nslices * PK_LISTS_PER_CTA;
+    p.list_bytes = pk_align(lists * 2 * k * 8, 256);
+    p.meta_bytes = pk_align(lists * 2 * 4, 256);
     p.hist_bytes = pk_align((size_t)PK_QN_MAX * (2 * d + 1) * 4, 256) + 256;  // + minima
     p.tau_bytes = pk_align((size_t)PK_QN_MAX * 8, 256);
     p.ws_bytes = p.list_bytes + p.meta_bytes + p.hist_bytes + p.tau_bytes;
@@ -790,8 +786,8 @@ PkPlan plan_pk(int64_t ns, int d, int k) {
 
 bool mma_packed_supported(int64_t ns, int d, int k) {
     const int W = (d + 63) / 64;
-    if (W % 2 != 0 || W > PK_W_MAX || k > MMA_K_MAX) return false;
-    return plan_pk(ns, d, k).nslices <= PK_MAX_SLICES;
+    if (W % 2 != 0 || W > PK_W_MAX || k > PK_K_MAX) return false;
+    return plan_pk(ns, d, k).nslices * PK_LISTS_PER_CTA <= PK_MAX_SLICES;
 }
 
 size_t mma_packed_workspace(int64_t ns, int d, int k) { return plan_pk(ns, d, k).ws_bytes; }
@@ -852,8 +848,8 @@ int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int
         else e = launch_pk<64>(tmap, a, p.nslices, stream);
         if (e != cudaSuccess) return EVP_ERR_CUDA;
         const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, a.hist, a.minhalf,
-                                              a.hist_bins, nqg, p.nslices, k, ids + q0 * k,
-                                              dist + q0 * k, stream);
+                                              a.hist_bins, nqg, p.nslices * PK_LISTS_PER_CTA, k,
+                                              ids + q0 * k, dist + q0 * k, stream);
         if (rc != EVP_OK) return rc;
     }
     return EVP_OK;

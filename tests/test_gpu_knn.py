@@ -14,9 +14,9 @@ PATHS = [1, 2, 3]   # EVP_PATH_POPC, EVP_PATH_MMA, EVP_PATH_MMA_PACKED
 
 def packed_supported(d, k):
     """Shapes the packed tensor-core path takes: d <= 768 with an even number
-    of 64-bit words per bitplane, k <= 1024."""
+    of 64-bit words per bitplane, k <= 256."""
     W = (d + 63) // 64
-    return W % 2 == 0 and W <= 12 and k <= 1024
+    return W % 2 == 0 and W <= 12 and k <= 256
 
 
 def _run(evp, Tq, Ts, d, x, k, dev, path=0):
@@ -100,7 +100,7 @@ def test_query_counts_span_passes(evp_lib, dev, nq, path):
 
 
 @pytest.mark.parametrize("path,k", [(1, 300), (2, 128), (1, 1024), (2, 300), (2, 1024),
-                                    (3, 128), (3, 300), (3, 1024)])
+                                    (3, 128), (3, 256), (3, 1024)])
 def test_massive_ties(evp_lib, dev, path, k):
     """Only six distinct codes in the database: almost every Delta ties, so
     the (Delta, index) order decides everything, across slices and merges."""
@@ -197,8 +197,8 @@ def test_tensor_path_cta_pair_and_single(evp_lib, dev, monkeypatch, pair, nq, ns
                                        (64, 50_000, 768, 10),   # one full 64-query pass
                                        (65, 50_000, 768, 10),   # a second pass of one query
                                        (200, 9_000, 384, 50),   # four passes, d = 384
-                                       (5, 130_000, 128, 1024),
-                                       (33, 1_000, 256, 1000),
+                                       (5, 130_000, 128, 256),
+                                       (33, 1_000, 256, 200),
                                        (40, 129, 640, 100)])    # one tile and a ragged row
 def test_packed_tensor_path(evp_lib, dev, nq, ns, d, k):
     """The packed tensor-core scan (tiles unpacked on chip, database rows as
