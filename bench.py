@@ -86,12 +86,16 @@ KERNEL_SOURCES = {
 MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 7_694_802_176 + 4_100_096,
-        "sources_sha256": "e9175fa019fa880ed8b8195809b7a395f0569b30db5a61151ba740108a774aec"},
+        "bytes": 7_684_182_272 + 4_177_664,
+        "sources_sha256": "0db5f379f00ea97c54f62b0b2116ef7e0217c7bc09dc36a838b67582f431f7ce"},
     # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
     ("scan_popc", 10_000_000, 768, 1, 100): {
-        "bytes": 1_920_047_616 + 3_326_976,
-        "sources_sha256": "08f0eb4023a2f101009c110d6158fdf9d2da78a63c1428e6faf98ed19e5457be"},
+        "bytes": 1_920_232_704 + 3_361_024,
+        "sources_sha256": "e890e277990be005e25ae483e6b095740f046a384bb3505d9d70a40b46d91ae0"},
+    # profiles/scan_mma_packed_10Mx768_b16.md (DRAM capture of the 16-query command)
+    ("scan_mma_packed", 10_000_000, 768, 16, 100): {
+        "bytes": 1_921_572_608 + 8_961_280,
+        "sources_sha256": "1e316739f7a77bb5621a34bb9e0487e4aa838e8cdbc4fbddf3b6f91390646617"},
 }
 
 
