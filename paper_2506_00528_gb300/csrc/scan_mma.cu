@@ -231,24 +231,31 @@ __device__ __forceinline__ int64_t query_of_lane(int m, int rank, int cg) {
     return (int64_t)j * cg + rank;
 }
 
-// Max-heap of u32 keys, element i of thread m at h[i * qa + m] (qa = active
-// queries per tile).
+// 4-ary max-heap of u32 keys, element i of thread m at h[i * qa + m] (qa =
+// active queries per tile); the children of i are 4i + 1 .. 4i + 4.  Half
+// the depth of a binary heap: a sift-down is a chain of about four
+// dependent shared-memory rounds (the four child loads are independent)
+// instead of seven for the 100 keys of a typical k.
 __device__ __forceinline__ void heap_sift_down(uint32_t* h, int qa, int m, int n, int i) {
     const uint32_t v = h[i * qa + m];
     while (true) {
-        int c = 2 * i + 1;
+        const int c = 4 * i + 1;
         if (c >= n) break;
         uint32_t cv = h[c * qa + m];
-        if (c + 1 < n) {
-            const uint32_t c2 = h[(c + 1) * qa + m];
-            if (c2 > cv) {
-                cv = c2;
-                ++c;
+        int best = c;
+#pragma unroll
+        for (int u = 1; u < 4; ++u) {
+            if (c + u < n) {
+                const uint32_t x = h[(c + u) * qa + m];
+                if (x > cv) {
+                    cv = x;
+                    best = c + u;
+                }
             }
         }
         if (cv <= v) break;
         h[i * qa + m] = cv;
-        i = c;
+        i = best;
     }
     h[i * qa + m] = v;
 }
@@ -256,7 +263,7 @@ __device__ __forceinline__ void heap_sift_down(uint32_t* h, int qa, int m, int n
 __device__ __forceinline__ void heap_push(uint32_t* h, int qa, int m, int n, uint32_t key) {
     int i = n;
     while (i > 0) {
-        const int p = (i - 1) >> 1;
+        const int p = (i - 1) >> 2;
         const uint32_t pv = h[p * qa + m];
         if (pv >= key) break;
         h[i * qa + m] = pv;
