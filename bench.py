@@ -86,8 +86,8 @@ KERNEL_SOURCES = {
 MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 7_684_139_008 + 4_282_880,
-        "sources_sha256": "23ea039115207d06b2b38ccc417f92ee1b2723eb679ede4753553c976897ac50"},
+        "bytes": 7_684_316_416 + 3_961_600,
+        "sources_sha256": "6ce1c8506b49d45be47a911e038d8285e6dccea727bf5b1f29feadf5cfbb6f63"},
     # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
     ("scan_popc", 10_000_000, 768, 1, 100): {
         "bytes": 1_920_232_704 + 3_361_024,

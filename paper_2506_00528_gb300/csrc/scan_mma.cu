@@ -63,8 +63,10 @@ constexpr int EPI_WARPS = 4;
 constexpr int A_STAGE_BYTES = MMA_M * KCHUNK;
 constexpr int HEAP_BYTES = HEAP_SLOTS * 4;
 constexpr int STAGE_SLOTS = 32;                     // per-thread candidate staging
-constexpr int FLUSH_AT = 8;   // staged keys that trigger a flush at the end of a tile
+constexpr int FLUSH_AT = 1;   // staged keys that trigger a flush at the end of a tile
 constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
+// A 32-column group can stage up to 32 keys per lane right after a flush.
+static_assert(STAGE_SLOTS >= 32, "staging must hold one full column group");
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
 constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
