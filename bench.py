@@ -86,8 +86,8 @@ KERNEL_SOURCES = {
 MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 7_684_316_416 + 3_961_600,
-        "sources_sha256": "6ce1c8506b49d45be47a911e038d8285e6dccea727bf5b1f29feadf5cfbb6f63"},
+        "bytes": 7_683_557_888 + 4_296_192,
+        "sources_sha256": "35070e6b6dd2870f20da59cb6e36bafcf1c7e57217298adf2d4e973e0224849d"},
     # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
     ("scan_popc", 10_000_000, 768, 1, 100): {
         "bytes": 1_920_232_704 + 3_361_024,
