@@ -116,3 +116,24 @@ def test_workspace_serves_every_smaller_batch(lib, d, ns):
                 w = f(nq, ns, d, k, path)
                 assert w >= prev, (path, k, nq)
                 prev = w
+
+
+def test_packed_path_limits_in_workspace_sizes(lib):
+    """The packed tensor-core path takes d <= 768 with an even number of
+    64-bit words per bitplane and k <= 256: outside those it needs no
+    workspace (a call is refused), inside it needs one pass's lists, the
+    same for every batch size, and the automatic path's bound covers it
+    from four queries up."""
+    f = lib.ternary_knn_path_workspace
+    f.restype = ctypes.c_size_t
+    f.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32]
+    ns = 1_000_000
+    for d in (65, 128, 384, 512, 768):              # W = 2, 2, 6, 8, 12
+        w = [f(nq, ns, d, 100, 3) for nq in (1, 16, 64, 65, 300)]
+        assert w[0] > 0 and len(set(w)) == 1, (d, w)
+        assert f(16, ns, d, 256, 3) > 0
+        assert f(16, ns, d, 257, 3) == 0
+        for nq in (4, 16, 64):
+            assert f(nq, ns, d, 100, 0) >= w[0]
+    for d in (64, 129, 700, 1024):                  # W = 1, 3, 11, 16
+        assert f(16, ns, d, 100, 3) == 0, d
