@@ -9,6 +9,8 @@
 * 10,000,000 x 1024, x = 256, 4,096 queries (the large dense contraction):
   the resident database's tensor-core scan, shortlist 100, rerank to 10,
   checked the same way.
+* 10,000,000 x 768, 16 queries on the packed tensor-core scan: identical to
+  the popcount scan and checked the same way on sampled rows.
 """
 import numpy as np
 import pytest
@@ -119,4 +121,38 @@ def test_dense_contraction_10m_1024_sampled(evp_lib, dev):
         g_local = np.array([[int(np.where(sl_h[q] == j)[0][0]) for j in gi]])
         local = np.arange(n_sl, dtype=np.int64)[None, :]
         check_rerank(g_local, rsc_h[q:q + 1], Q_h[q:q + 1], rows, local, k)
+    db.close()
+
+
+def test_packed_path_10m_16_queries_sampled(evp_lib, dev):
+    """The packed tensor-core scan at the full 10M x 768 size with 16
+    queries (the launch `bench.py --batch 16` times): results identical to
+    the popcount scan's, and checked against the oracle on sampled rows."""
+    n, d, x, nq, k = 10_000_000, 768, 512, 16, 100
+    U = synth.mixture_torch(n, d, n_centres=1024, anisotropic=True, stream=synth.STREAM_DB,
+                            device=dev)
+    Q = synth.mixture_torch(nq, d, n_centres=1024, anisotropic=True,
+                            stream=synth.STREAM_QUERIES, device=dev)
+    st = evp_lib.new_status(dev)
+    Ts = evp_lib.encode(U, x, status=st)
+    Tq = evp_lib.encode(Q, x, status=st)
+    db = evp_lib.Database(Ts, None, d, x, tensor_copy=False)
+    ids, dist = db.knn(Tq, k, status=st, path=3)
+    ids_a, dist_a = db.knn(Tq, k, status=st)          # the automatic choice (packed here)
+    ids_p, dist_p = db.knn(Tq, k, status=st, path=1)  # the popcount scan
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert torch.equal(ids, ids_p) and torch.equal(dist, dist_p)
+    assert torch.equal(ids, ids_a) and torch.equal(dist, dist_a)
+    rng = np.random.default_rng(654)
+    sample_idx = np.sort(rng.choice(n, 40_000, replace=False))
+    U_sample = U[torch.from_numpy(sample_idx).to(dev)].cpu().numpy()
+    V_sample = par_encode(U_sample, x)
+    Q_h = Q.cpu().numpy()
+    sel = (0, 7, 15)
+    Vq = oracle.encode(Q_h[list(sel)], x)
+    ids_h, dist_h = ids.cpu().numpy(), dist.cpu().numpy()
+    for i, q in enumerate(sel):
+        rows = U[torch.from_numpy(ids_h[q]).to(dev)].cpu().numpy()
+        check_knn_sampled(Vq[i], ids_h[q], dist_h[q], oracle.encode(rows, x), V_sample, sample_idx)
     db.close()
