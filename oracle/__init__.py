@@ -15,6 +15,15 @@ Each function follows a passage of the paper (arXiv 2506.00528):
 * ``knn``        -- Sec. 5.3 / Table 5: exhaustive kNN, (Delta, index) order.
 * ``rerank``     -- Sec. 5.3: re-order an n-long shortlist by the original
   float vectors (double-precision scalar product), keep the best k.
+* ``quantize_i8`` -- Sec. 6 (single-operand translation): the query kept as
+  int8 by symmetric per-query scaling (a reading; the paper fixes no
+  precision for the untranslated operand).
+* ``masked_sum`` / ``knn_i8q`` -- Sec. 5.1.2 masked addition of a query over
+  a ternary code; exhaustive search by that score (largest first).
+* ``sparse_pack``/``sparse_unpack`` -- Sec. 6 ("different EVPs"): a code with
+  few non-zeros stored as the list of its non-zero dimensions.
+* ``l2_knn``     -- the float32 "Euclidean" brute force the paper's speed
+  tables compare against (Tables 4 and 5); a CPU baseline, not the method.
 
 The arithmetic lives in ``evp_oracle.c`` (C99, single thread); this module
 only marshals numpy arrays.  ``build()`` compiles it with gcc.
@@ -76,6 +85,18 @@ def _load():
             lib.evpo_rerank.restype = _i32
             lib.evpo_rerank.argtypes = [_p, _i64, _p, _i64, _i32, _p, _i32, _i32,
                                         _p, _p, _p]
+            lib.evpo_quantize_i8.restype = _i32
+            lib.evpo_quantize_i8.argtypes = [_p, _i64, _i32, _p]
+            lib.evpo_masked_sum.restype = _i64
+            lib.evpo_masked_sum.argtypes = [_p, _p, _i32]
+            lib.evpo_knn_i8q.restype = _i32
+            lib.evpo_knn_i8q.argtypes = [_p, _i64, _p, _i64, _i32, _i32, _p, _p]
+            lib.evpo_sparse_pack.restype = _i64
+            lib.evpo_sparse_pack.argtypes = [_p, _i64, _i32, _i32, _p]
+            lib.evpo_sparse_unpack.restype = _i64
+            lib.evpo_sparse_unpack.argtypes = [_p, _i64, _i32, _i32, _p]
+            lib.evpo_l2_knn.restype = _i32
+            lib.evpo_l2_knn.argtypes = [_p, _i64, _p, _i64, _i32, _i32, _p, _p]
             _lib = lib
     return _lib
 
@@ -192,3 +213,75 @@ def rerank(Q: np.ndarray, S: np.ndarray, shortlist: np.ndarray, k: int):
     if rc != 0:
         raise ValueError("shortlist id out of range")
     return ids, scores, absdot
+
+
+def quantize_i8(Q: np.ndarray, allow_nonfinite: bool = False) -> np.ndarray:
+    """Per-query symmetric int8 quantisation (Sec. 6 reading): float32 [n, d] -> int8."""
+    Q = _c(Q, np.float32)
+    n, d = Q.shape
+    out = np.zeros((n, d), dtype=np.int8)
+    bad = _load().evpo_quantize_i8(_ptr(Q), n, d, _ptr(out))
+    if bad and not allow_nonfinite:
+        raise NonFiniteInput("non-finite value in query rows")
+    return out
+
+
+def masked_sum(q8: np.ndarray, v: np.ndarray) -> int:
+    """Masked addition (Sec. 5.1.2): sum of q8 where v = +1 minus where v = -1."""
+    q8 = _c(q8, np.int8).ravel()
+    v = _c(v, np.int8).ravel()
+    assert q8.size == v.size
+    return int(_load().evpo_masked_sum(_ptr(q8), _ptr(v), q8.size))
+
+
+def knn_i8q(Q8: np.ndarray, Vs: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Exhaustive search by masked-addition score: ids int64, score int32 [nq, k],
+    largest score first, equal scores by lower index."""
+    Q8 = _c(Q8, np.int8)
+    Vs = _c(Vs, np.int8)
+    nq, d = Q8.shape
+    ns = Vs.shape[0]
+    assert Vs.shape[1] == d
+    if not 1 <= k <= ns:
+        raise ValueError("k must satisfy 1 <= k <= ns")
+    ids = np.zeros((nq, k), dtype=np.int64)
+    score = np.zeros((nq, k), dtype=np.int32)
+    if _load().evpo_knn_i8q(_ptr(Q8), nq, _ptr(Vs), ns, d, int(k), _ptr(ids), _ptr(score)):
+        raise MemoryError("oracle knn_i8q failed")
+    return ids, score
+
+
+def sparse_pack(V: np.ndarray, x: int) -> np.ndarray:
+    """Ternary int8 [n, d] with x non-zeros per row -> uint16 [n, x] index lists
+    (bit 15 = -1, bits 0-14 = dimension, ascending)."""
+    V = _c(V, np.int8)
+    n, d = V.shape
+    E = np.zeros((n, int(x)), dtype=np.uint16)
+    bad = _load().evpo_sparse_pack(_ptr(V), n, d, int(x), _ptr(E))
+    if bad:
+        raise ValueError(f"{bad} rows do not have exactly x non-zeros")
+    return E
+
+
+def sparse_unpack(E: np.ndarray, d: int) -> tuple[np.ndarray, int]:
+    """Index lists uint16 [n, x] -> ternary int8 [n, d]; also the number of
+    malformed rows."""
+    E = _c(E, np.uint16)
+    n, x = E.shape
+    V = np.zeros((n, int(d)), dtype=np.int8)
+    bad = _load().evpo_sparse_unpack(_ptr(E), n, int(d), int(x), _ptr(V))
+    return V, int(bad)
+
+
+def l2_knn(Q: np.ndarray, S: np.ndarray, k: int) -> tuple[np.ndarray, np.ndarray]:
+    """Float32 exhaustive kNN by squared Euclidean distance (the paper's
+    "Euclidean" speed baseline): ids int64, dist float32 [nq, k]."""
+    Q = _c(Q, np.float32)
+    S = _c(S, np.float32)
+    nq, d = Q.shape
+    ns = S.shape[0]
+    ids = np.zeros((nq, k), dtype=np.int64)
+    dist = np.zeros((nq, k), dtype=np.float32)
+    if _load().evpo_l2_knn(_ptr(Q), nq, _ptr(S), ns, d, int(k), _ptr(ids), _ptr(dist)):
+        raise ValueError("oracle l2_knn failed")
+    return ids, dist

@@ -286,3 +286,189 @@ int evpo_rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int d,
     free(c);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* Single-operand translation (Sec. 6): only the database is mapped to  */
+/* EVP vertices; the query keeps (almost) its original values.  Here     */
+/* the query is held as int8 so that every score stays an exact integer. */
+/* The paper does not fix this precision; the reading used is symmetric  */
+/* per-query scaling: m = max_i |q_i|, scale = 127 / m (float32), and    */
+/* q8_i = q_i * scale rounded to the nearest integer, ties to even, all  */
+/* in float32 (m = 0 gives the zero vector).  Returns 1 if some q_i is   */
+/* NaN or infinite (that row is then left zero), 0 otherwise.            */
+/* ------------------------------------------------------------------ */
+int evpo_quantize_i8(const float* Q, int64_t nq, int d, int8_t* Q8)
+{
+    int64_t r;
+    int j, bad = 0;
+    for (r = 0; r < nq; ++r) {
+        const float* q = Q + r * (int64_t)d;
+        int8_t* o = Q8 + r * (int64_t)d;
+        float m = 0.0f, scale;
+        int finite = 1;
+        for (j = 0; j < d; ++j) {
+            float a = fabsf(q[j]);
+            if (!(a <= 3.4028234663852886e38f)) finite = 0;   /* NaN or infinity */
+            else if (a > m) m = a;
+        }
+        if (!finite) {
+            for (j = 0; j < d; ++j) o[j] = 0;
+            bad = 1;
+            continue;
+        }
+        if (m == 0.0f) {
+            for (j = 0; j < d; ++j) o[j] = 0;
+            continue;
+        }
+        scale = 127.0f / m;
+        for (j = 0; j < d; ++j) {
+            float p = q[j] * scale;
+            o[j] = (int8_t)rintf(p);
+        }
+    }
+    return bad;
+}
+
+/* Masked addition (Sec. 5.1.2): the scalar product of a query with a    */
+/* ternary vector v needs no multiplication -- the query elements where  */
+/* v is +1 are added and those where v is -1 subtracted.  Exhaustive     */
+/* search with that score (Sec. 5.3 with the single-operand translation */
+/* of Sec. 6): per query the k rows with the largest score, equal scores */
+/* by lower row index.                                                  */
+int64_t evpo_masked_sum(const int8_t* q8, const int8_t* v, int d)
+{
+    int64_t s = 0;
+    int j;
+    for (j = 0; j < d; ++j) {
+        if (v[j] == 1) s += q8[j];
+        else if (v[j] == -1) s -= q8[j];
+    }
+    return s;
+}
+
+int evpo_knn_i8q(const int8_t* Q8, int64_t nq, const int8_t* Vs, int64_t ns, int d,
+                 int k, int64_t* ids, int32_t* score)
+{
+    evpo_cand_t* all;
+    int64_t q, s;
+    int j;
+    if (nq <= 0) return 0;
+    if (k < 1 || (int64_t)k > ns) return -1;
+    all = (evpo_cand_t*)malloc(sizeof(evpo_cand_t) * (size_t)ns);
+    if (!all) return -1;
+    for (q = 0; q < nq; ++q) {
+        const int8_t* q8 = Q8 + q * (int64_t)d;
+        for (s = 0; s < ns; ++s) {
+            /* ascending (-score, index) = descending score, lower index first */
+            all[s].delta = -evpo_masked_sum(q8, Vs + s * (int64_t)d, d);
+            all[s].idx = s;
+        }
+        qsort(all, (size_t)ns, sizeof(evpo_cand_t), evpo_cmp_cand);
+        for (j = 0; j < k; ++j) {
+            ids[q * k + j] = all[j].idx;
+            score[q * k + j] = (int32_t)(-all[j].delta);
+        }
+    }
+    free(all);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Sparse representation for small x (Sec. 6, "different EVPs": fewer    */
+/* non-zeros).  A code is the list of its x non-zero dimensions in       */
+/* ascending order, each a 16-bit entry: bits 0-14 the dimension, bit 15 */
+/* set for -1.  Requires d <= 32768.  Returns the number of rows whose   */
+/* count of non-zeros is not x (those rows are left zero-filled).        */
+/* ------------------------------------------------------------------ */
+int64_t evpo_sparse_pack(const int8_t* V, int64_t n, int d, int x, uint16_t* E)
+{
+    int64_t r, bad = 0;
+    int j, c;
+    for (r = 0; r < n; ++r) {
+        const int8_t* v = V + r * (int64_t)d;
+        uint16_t* e = E + r * (int64_t)x;
+        for (c = 0, j = 0; j < d; ++j)
+            if (v[j] != 0) c++;
+        if (c != x) {
+            for (j = 0; j < x; ++j) e[j] = 0;
+            bad++;
+            continue;
+        }
+        for (c = 0, j = 0; j < d; ++j) {
+            if (v[j] == 1) e[c++] = (uint16_t)j;
+            else if (v[j] == -1) e[c++] = (uint16_t)(0x8000u | (unsigned)j);
+        }
+    }
+    return bad;
+}
+
+/* Inverse of evpo_sparse_pack; returns the number of malformed rows (a  */
+/* dimension >= d, or entries not strictly ascending).                   */
+int64_t evpo_sparse_unpack(const uint16_t* E, int64_t n, int d, int x, int8_t* V)
+{
+    int64_t r, bad = 0;
+    int j;
+    for (r = 0; r < n; ++r) {
+        const uint16_t* e = E + r * (int64_t)x;
+        int8_t* v = V + r * (int64_t)d;
+        int prev = -1, row_bad = 0;
+        for (j = 0; j < d; ++j) v[j] = 0;
+        for (j = 0; j < x; ++j) {
+            int dim = (int)(e[j] & 0x7FFFu);
+            if (dim >= d || dim <= prev) { row_bad = 1; break; }
+            v[dim] = (e[j] & 0x8000u) ? (int8_t)-1 : (int8_t)1;
+            prev = dim;
+        }
+        if (row_bad) bad++;
+    }
+    return bad;
+}
+
+/* ------------------------------------------------------------------ */
+/* The float baseline of the paper's speed comparison ("Euclidean" in    */
+/* Tables 4 and 5): exhaustive kNN by squared Euclidean distance over    */
+/* the original float32 vectors, summed in float32 in index order, the  */
+/* k smallest (distance, index) pairs ascending.  A CPU baseline, not    */
+/* part of the method.                                                  */
+/* ------------------------------------------------------------------ */
+typedef struct { float dist; int64_t idx; } evpo_fcand_t;
+
+static int evpo_cmp_fcand(const void* pa, const void* pb)
+{
+    const evpo_fcand_t* a = (const evpo_fcand_t*)pa;
+    const evpo_fcand_t* b = (const evpo_fcand_t*)pb;
+    if (a->dist != b->dist) return a->dist < b->dist ? -1 : 1;
+    return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
+}
+
+int evpo_l2_knn(const float* Q, int64_t nq, const float* S, int64_t ns, int d, int k,
+                int64_t* ids, float* dist)
+{
+    evpo_fcand_t* all;
+    int64_t q, s;
+    int j;
+    if (nq <= 0) return 0;
+    if (k < 1 || (int64_t)k > ns) return -1;
+    all = (evpo_fcand_t*)malloc(sizeof(evpo_fcand_t) * (size_t)ns);
+    if (!all) return -1;
+    for (q = 0; q < nq; ++q) {
+        const float* qv = Q + q * (int64_t)d;
+        for (s = 0; s < ns; ++s) {
+            const float* sv = S + s * (int64_t)d;
+            float acc = 0.0f;
+            for (j = 0; j < d; ++j) {
+                float e = qv[j] - sv[j];
+                acc += e * e;
+            }
+            all[s].dist = acc;
+            all[s].idx = s;
+        }
+        qsort(all, (size_t)ns, sizeof(evpo_fcand_t), evpo_cmp_fcand);
+        for (j = 0; j < k; ++j) {
+            ids[q * k + j] = all[j].idx;
+            dist[q * k + j] = all[j].dist;
+        }
+    }
+    free(all);
+    return 0;
+}
