@@ -144,22 +144,25 @@ int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns
 /* ---------------------------------------------------------------------
  * ternary_knn_static -- ternary_knn (popcount path) that allocates
  * nothing.  The paper has no counterpart; this exists for callers that
- * cannot allocate device memory: code running inside a CUDA graph capture
- * (where cudaMalloc is not allowed), serving threads that must never enter
- * the device allocator, plugins handed raw device pointers by a host that
- * owns all allocation, and plain C callers with no allocator.  Inputs and
- * outputs are the caller's, as in ternary_knn; the workspace is a fixed
+ * cannot allocate device memory: serving threads that must never enter the
+ * device allocator (an allocation can wait on device-wide
+ * synchronisation and so stall a latency-bound loop), plugins handed raw
+ * device pointers by a host framework that owns all allocation, and plain
+ * C callers with no allocator of their own.  Inputs and outputs are the
+ * caller's, as in ternary_knn; the workspace is a fixed
  * EVP_STATIC_SCRATCH_BYTES (16 MiB) array inside the library, present on
- * every GPU that loads it.  A request whose popcount-path workspace
- * (ternary_knn_path_workspace(nq, ns, d, k, EVP_PATH_POPC)) exceeds that
- * size is rejected with EVP_ERR_NO_MEMORY before anything is launched.
- * The first call on each device looks up the array's device address (with
- * that device current) and caches it, so make that first call before any
- * stream capture that includes this entry point.  All calls share the one
- * array and it keeps the previous call's contents (each call re-initialises
- * what it reads): calls that overlap on the GPU race on it, so the caller
- * must order them (one stream, or events).  Results are identical to
- * ternary_knn with EVP_PATH_POPC.
+ * every GPU that loads it until the process exits.  A request whose
+ * popcount-path workspace (ternary_knn_path_workspace(nq, ns, d, k,
+ * EVP_PATH_POPC)) exceeds that size is rejected with EVP_ERR_NO_MEMORY
+ * before anything is launched.  The first call on each device looks up the
+ * array's device address (with that device current) and caches it, so make
+ * that first call before any stream capture; a device reset
+ * (cudaDeviceReset) reloads the library's device code and invalidates the
+ * cached address, so the entry point must not be used after one.  All
+ * calls share the one array and it keeps the previous call's contents (each
+ * call re-initialises what it reads): calls that overlap on the GPU race on
+ * it, so the caller must order them (one stream, or events).  Results are
+ * identical to ternary_knn with EVP_PATH_POPC.
  * ------------------------------------------------------------------- */
 #define EVP_STATIC_SCRATCH_BYTES (16u << 20)
 int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns,
@@ -452,6 +455,45 @@ int32_t evp_server_destroy(evp_server_t s);
 int32_t evp_timing_enable(int32_t on);
 int32_t evp_timing_reset(void);
 int32_t evp_timing_read(const char* name, int64_t* launches, double* total_ms);
+
+/* ---------------------------------------------------------------------
+ * evp_probe_tensor_rate -- measured dense tensor-core rate (measurement
+ * support for the roofline of the tensor-core scans; the paper has no
+ * counterpart).
+ *
+ * Every SM (kind 0: tcgen05.mma.kind::f8f6f4 with e4m3 operands, K = 32;
+ * kind 1: kind::f16 with bf16 operands, K = 16; float32 accumulation)
+ * issues `iters` instructions of shape M x n x K back to back from one
+ * thread, on operands resident in shared memory that hold +1, -1 and 0 in
+ * equal shares (the values the scans contract).  cta_pair = 0: one CTA per
+ * SM, M = 128; cta_pair = 1: CTA pairs (cta_group::2), M = 256.  n is a
+ * multiple of 16 in [16, 256]; 1 <= iters <= 2^26.  Synchronous: the launch
+ * is timed with CUDA events on `stream`.  Outputs: *tflops =
+ * 2 M n K iters x instruction issuers / elapsed time; *cycles_per_mma =
+ * SM clocks per instruction on the issuing thread (averaged over SMs);
+ * *ms = elapsed time.  (The int8 kind, kind::i8, does not exist on sm_103a:
+ * ptxas rejects it for this target.)  Returns EVP_OK, EVP_ERR_INVALID,
+ * EVP_ERR_NO_MEMORY (two small device buffers), EVP_ERR_TIMEOUT or
+ * EVP_ERR_CUDA.
+ * ------------------------------------------------------------------- */
+int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t iters,
+                              double* tflops, double* cycles_per_mma, double* ms, void* stream);
+
+/* ---------------------------------------------------------------------
+ * Testing support for failure detection (the paper has no counterpart).
+ *
+ * evp_test_stall_producer(path, fills) arms a one-shot stall for the next
+ * launch of the tensor-core scan `path` (EVP_PATH_MMA or
+ * EVP_PATH_MMA_PACKED): the first CTA's copy producer stops after `fills`
+ * stage fills, as a copy engine that never delivers would.  The scan's
+ * bounded device waits (2 s) then expire: the call writes EVP_ERR_TIMEOUT
+ * to dev_status, every CTA waits (bounded) for the copies and tensor-core
+ * operations it issued, frees its tensor memory and exits, the outputs
+ * are unspecified, and the device stays usable for later calls.  Nothing
+ * faults.  fills < 0 disarms.  Returns EVP_OK, or EVP_ERR_INVALID for
+ * another path.
+ * ------------------------------------------------------------------- */
+int32_t evp_test_stall_producer(int32_t path, int32_t fills);
 
 #ifdef __cplusplus
 }

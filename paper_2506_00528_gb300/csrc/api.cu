@@ -2,6 +2,7 @@
 // checks on the host, then kernel launches on the caller's stream.
 #include "evp_internal.cuh"
 
+#include <atomic>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -33,6 +34,14 @@ int num_sms() {
     }
     return cached[dev];
 }
+
+// ---- testing support: a stalled copy producer ------------------------------
+namespace {
+std::atomic<int> g_stall_mma{-1}, g_stall_packed{-1};
+}  // namespace
+
+int take_stall_mma() { return g_stall_mma.exchange(-1); }
+int take_stall_packed() { return g_stall_packed.exchange(-1); }
 
 // ---- kernel timing ------------------------------------------------------
 namespace {
@@ -244,6 +253,13 @@ int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d
     cudaError_t e = launch_rerank(Q, nq, S, ns, d, shortlist, n, k, ids, scores, dev_status,
                                   static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+int32_t evp_test_stall_producer(int32_t path, int32_t fills) {
+    if (path == EVP_PATH_MMA) evp::g_stall_mma.store(fills < 0 ? -1 : fills);
+    else if (path == EVP_PATH_MMA_PACKED) evp::g_stall_packed.store(fills < 0 ? -1 : fills);
+    else return EVP_ERR_INVALID;
+    return EVP_OK;
 }
 
 int32_t evp_timing_enable(int32_t on) {

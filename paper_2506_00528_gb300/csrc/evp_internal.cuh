@@ -61,6 +61,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// Count `bytes` of transactions as done on a barrier of this CTA without a
+// copy (accounts for a copy that was expected but will never be issued).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
 // One arrival on a barrier of this CTA.
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -225,6 +234,12 @@ struct TimedLaunch {
 
 // ---- launchers (defined in the .cu files, called from api.cu) ----------
 int num_sms();
+
+// Testing support (evp_test_stall_producer): stage fills after which the
+// next launch of a tensor-core scan stops its first CTA's copy producer;
+// -1 = none.  take_* returns the armed value and disarms it.
+int take_stall_mma();
+int take_stall_packed();
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (the
 // library does not link libcuda directly).  nullptr if unavailable.

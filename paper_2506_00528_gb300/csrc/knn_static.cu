@@ -2,13 +2,12 @@
 // device array owned by this library, for callers that cannot allocate
 // device memory.
 //
-// Who needs it: code that runs where cudaMalloc is unavailable or
-// forbidden -- inside a CUDA graph capture region, on a latency-critical
-// serving thread that must never enter the device allocator (which can
-// block on device-wide synchronisation), in a plugin that is handed raw
-// device pointers by a host framework that owns all allocation, or in C
-// callers that have no allocator of their own.  Those callers still pass
-// their inputs and outputs; only the workspace comes from here.
+// Who needs it: code that must not or cannot allocate device memory -- a
+// latency-critical serving thread that must never enter the device
+// allocator (which can block on device-wide synchronisation), a plugin that
+// is handed raw device pointers by a host framework that owns all
+// allocation, or a C caller that has no allocator of its own.  Those callers
+// still pass their inputs and outputs; only the workspace comes from here.
 //
 // The scratch is one file-scope __device__ array of EVP_STATIC_SCRATCH_BYTES
 // (16 MiB), present on every GPU that loads the library until the process
@@ -16,7 +15,8 @@
 // the first call on each device the library asks the runtime for the
 // array's device address (cudaGetSymbolAddress, with that device current)
 // and caches it.  That first call on a device should therefore happen
-// before any stream capture that includes this entry point.
+// before any stream capture.  A device reset reloads the device code and
+// invalidates the cached address; the entry point is not for use after one.
 //
 // Every call shares the one array: calls that overlap on the GPU (two
 // streams, or two host threads) race on it and must be ordered by the

@@ -42,8 +42,8 @@
 // lists go to the workspace and the per-query merge of the popcount path
 // combines them.  Every mbarrier wait is bounded (2 s); on expiry the CTA
 // reports EVP_ERR_TIMEOUT, raises an abort flag in itself and its pair
-// peer (every other wait then gives up at once), lets the copies and MMAs
-// already issued land, and frees TMEM.
+// peer (every other wait then gives up at once), waits (bounded) for the
+// copies and MMAs already issued to complete, and frees TMEM.
 #include "evp_internal.cuh"
 
 #include <algorithm>
@@ -113,6 +113,7 @@ struct MmaArgs {
     uint32_t* minhalf;     // [nq]: smallest Delta/2 any slice inserted
     int hist_bins;         // 2x + 1
     int32_t* status;
+    int stall_fills;       // testing: CTA 0's producer stops after this many fills (-1: never)
 };
 
 // Maximum of three floats in one instruction (no NaN among the inputs here).
@@ -300,6 +301,8 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
     int* cur_item = abort_flag + 1;   // item the epilogue is on
     int* epi_done = abort_flag + 2;   // epilogue finished (helper stops)
+    int* fills = abort_flag + 3;      // stage fills this CTA's producer issued
+    int* peer_fills = abort_flag + 4; // CG = 2: the same count of the other CTA
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nslices = a.nslices;
@@ -340,6 +343,8 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         *abort_flag = 0;
         *cur_item = -1;
         *epi_done = 0;
+        *fills = 0;
+        *peer_fills = 0;
         fence_mbar_init();
     }
     for (int i = threadIdx.x; i < MMA_M; i += NUM_THREADS) ubound[i] = ~0ull;
@@ -386,6 +391,16 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     for (int kc = 0; kc < kchunks; ++kc, ++it) {
                         const int s = it % STAGES;
                         const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                        if (it == a.stall_fills && blockIdx.x == 0) {
+                            // testing: a producer that stops issuing copies, so
+                            // that the consumers' bounded waits expire
+                            const uint64_t t0 = globaltimer_ns();
+                            while (!*(volatile int*)abort_flag &&
+                                   globaltimer_ns() - t0 < 2 * WAIT_LIMIT_NS)
+                                __nanosleep(1000);
+                            ok = false;
+                            break;
+                        }
                         if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, abort_flag)) {
                             ok = false;
                             break;
@@ -415,6 +430,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 if (!*(volatile int*)abort_flag) report(a.status, EVP_ERR_TIMEOUT);
                 raise_abort();
             }
+            *fills = it;
         }
     } else if (warp == 1) {
         if (lane == 0 && leader) {
@@ -708,14 +724,35 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
     tc_fence_before();
     __syncthreads();
-    if (*(volatile int*)abort_flag && threadIdx.x == 0) {
-        // after an abort, copies and MMAs already issued into this CTA's
-        // shared memory may still be in flight: give them time to land
-        const uint64_t t0 = globaltimer_ns();
-        while (globaltimer_ns() - t0 < 5000000ull) __nanosleep(10000);
+    if constexpr (CG == 2) {
+        // each CTA tells the other how many stage fills its producer issued
+        if (threadIdx.x == 0) st_cluster_u32(peer_addr(peer_fills, rank ^ 1u), (uint32_t)*fills);
+        cluster_sync_all();
+    }
+    if (*(volatile int*)abort_flag && threadIdx.x == 0 && leader) {
+        // After an abort, copies issued into either CTA's stages may still be
+        // in flight; every copy of fill j signals the leader's full barrier
+        // of stage j % STAGES.  A fill could only be issued once the fill
+        // STAGES before it had completed, so only the last STAGES fills of
+        // the two producers can be pending: wait (bounded) for each of them,
+        // first completing the accounting of a fill that one CTA of the pair
+        // issued and the other did not (its expected bytes never come, or
+        // its arrival never happened).  The MMA issuer has already waited
+        // for every MMA it issued.
+        const int own = *fills;
+        const int other = CG == 2 ? *peer_fills : own;
+        const int hi = max(own, other);
+        for (int j = max(0, hi - STAGES); j < hi; ++j) {
+            const int s = j % STAGES;
+            if constexpr (CG == 2) {
+                if (j >= own) mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                else if (j >= other) mbar_complete_tx(&full[s], STAGE_BYTES);
+            }
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) break;
+        }
     }
     __syncthreads();
-    if constexpr (CG == 2) cluster_sync_all();  // no arrivals into the peer remain
+    if constexpr (CG == 2) cluster_sync_all();  // no copies or arrivals into the peer remain
     tc_fence_after();
     if (warp == 1) {
         if constexpr (CG == 1)
@@ -941,6 +978,7 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.minhalf = minhalf;
     args.hist_bins = hist_bins;
     args.status = status;
+    args.stall_fills = take_stall_mma();
     const int items = (p.qtiles + p.cg - 1) / p.cg * p.nslices;
     if (p.cg == 1) {
         if (cudaFuncSetAttribute(scan_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -98,6 +98,7 @@ struct PkArgs {
     uint32_t* minhalf;     // [PK_QN_MAX]
     int hist_bins;         // 2x + 1
     int32_t* status;
+    int stall_fills;  // testing: CTA 0's producer stops after this many fills (-1: never)
 };
 
 __host__ __device__ inline size_t pk_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -125,7 +126,7 @@ __host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn) {
     L.ub_off = L.thr_off + states * 4;
     L.cnt_off = L.ub_off + (size_t)qn * 4;
     L.bar_off = pk_align(L.cnt_off + 4 * states * 4, 8);
-    L.misc_off = L.bar_off + (size_t)(2 * stages + 6) * 8;
+    L.misc_off = L.bar_off + (size_t)(2 * stages + 7) * 8;
     L.total = L.misc_off + 16 + 1024;
     return L;
 }
@@ -300,6 +301,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
     uint64_t* d_full = bars + 2 * S + 2;   // [2]  MMA -> epilogue and unpack warps (tile's
                                            //      MMAs complete: accumulator ready, A read)
     uint64_t* d_empty = bars + 2 * S + 4;  // [2]  epilogue -> MMA (accumulator read)
+    uint64_t* done = bars + 2 * S + 6;     // [1]  every MMA issued has completed
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L.misc_off);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
     int* epi_done = abort_flag + 1;        // epilogue warps finished (the helper stops at 8)
@@ -324,6 +326,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             mbar_init(&d_full[b], 1);
             mbar_init(&d_empty[b], PK_EPI_WARPS);
         }
+        mbar_init(done, 1);
         *abort_flag = 0;
         *epi_done = 0;
         fence_mbar_init();
@@ -388,6 +391,15 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             int t = 0;
             for (; t < ntl; ++t) {
                 const int s = t % S;
+                if (t == a.stall_fills && blockIdx.x == 0) {
+                    // testing: a producer that stops issuing copies, so that
+                    // the consumers' bounded waits expire
+                    const uint64_t t0 = globaltimer_ns();
+                    while (!*(volatile int*)abort_flag && globaltimer_ns() - t0 < 2 * WAIT_LIMIT_NS)
+                        __nanosleep(1000);
+                    ok = false;
+                    break;
+                }
                 if (t >= S &&
                     !mbar_wait_or_abort(&empty[s], (uint32_t)(((t / S) - 1) & 1), abort_flag)) {
                     ok = false;
@@ -436,6 +448,9 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                 mma_commit(&d_full[b]);  // one commit per tile: each drains the MMA pipe
             }
             if (!ok) give_up();
+            // every MMA issued completes before tensor memory is released
+            mma_commit(done);
+            if (!mbar_wait_bounded(done, 0)) give_up();
         }
     } else if (warp < PK_UNPACK_WARPS) {
         // ---------------- unpack warps ----------------
@@ -717,14 +732,9 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         }
     }
 
+    // The producer has waited for every copy it issued and the MMA issuer
+    // for every MMA (bounded, also after an abort).
     tc_fence_before();
-    __syncthreads();
-    if (*(volatile int*)abort_flag && tid == 0) {
-        // after an abort, MMAs already issued may still be running: give
-        // them time to finish before TMEM is released
-        const uint64_t t0 = globaltimer_ns();
-        while (globaltimer_ns() - t0 < 5000000ull) __nanosleep(10000);
-    }
     __syncthreads();
     tc_fence_after();
     if (warp == PK_MMA_WARP)
@@ -829,6 +839,7 @@ int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int
     a.tau_global = reinterpret_cast<uint64_t*>(w + p.list_bytes + p.meta_bytes + p.hist_bytes);
     a.hist_bins = 2 * x + 1;
     a.status = status;
+    a.stall_fills = take_stall_packed();
 
     for (int64_t q0 = 0; q0 < nq; q0 += PK_QN_MAX) {
         const int nqg = (int)std::min<int64_t>(PK_QN_MAX, nq - q0);

@@ -427,12 +427,16 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
     const int64_t q = blockIdx.x;
     const int64_t qbase = q * nslices;
 
-    for (int s = tid; s < nslices; s += FM_THREADS) lens[s] = meta[(qbase + s) * 2];
+    // Lengths and buffer indices are clamped to the list storage: after a
+    // scan that gave up (EVP_ERR_TIMEOUT) some of them were never written,
+    // and the merge must still stay inside the workspace.
+    for (int s = tid; s < nslices; s += FM_THREADS)
+        lens[s] = min(max(meta[(qbase + s) * 2], 0), k);
     __syncthreads();
     bool staged_now = false;
     auto list_ptr = [&](int s) -> const uint64_t* {
         return staged_now ? staged + (int64_t)s * k
-                          : lists + ((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k;
+                          : lists + ((qbase + s) * 2 + (meta[(qbase + s) * 2 + 1] & 1)) * k;
     };
     auto count_le = [&](uint64_t v) -> int {
         int c = 0;
@@ -490,7 +494,7 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
         if (stage_lists) {
             for (int64_t e = tid; e < (int64_t)nslices * k; e += FM_THREADS) {
                 const int s = (int)(e / k), i = (int)(e - (int64_t)s * k);
-                if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + meta[(qbase + s) * 2 + 1]) * k + i];
+                if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + (meta[(qbase + s) * 2 + 1] & 1)) * k + i];
             }
             __syncthreads();
             staged_now = true;

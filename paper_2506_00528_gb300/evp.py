@@ -86,6 +86,10 @@ SIGNATURES = {
     "evp_batch_plan_workspace": (_sz, [_p]),
     "evp_batch_run": (_i32, [_p, _p, _p]),
     "evp_batch_plan_destroy": (_i32, [_p]),
+    "evp_test_stall_producer": (_i32, [_i32, _i32]),
+    "evp_probe_tensor_rate": (_i32, [_i32, _i32, _i32, _i64, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), _p]),
     "evp_timing_enable": (_i32, [_i32]),
     "evp_timing_reset": (_i32, []),
     "evp_timing_read": (_i32, [ctypes.c_char_p, ctypes.POINTER(ctypes.c_int64),
@@ -211,6 +215,15 @@ def ternary_knn_static(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
     (no allocation by the library; outputs must be given)."""
     _req(Q, torch.int64, "Q")
     _req(S, torch.int64, "S")
+    _req(ids, torch.int64, "ids")
+    _req(dist, torch.int32, "dist")
+    nq = Q.shape[0]
+    if Q.dim() != 2 or S.dim() != 2 or Q.shape[1] != 2 * words(d) or S.shape[1] != Q.shape[1]:
+        raise ValueError("Q and S must be [n, 2W] packed codes for this d")
+    if tuple(ids.shape) != (nq, int(k)) or tuple(dist.shape) != (nq, int(k)):
+        raise ValueError(f"ids and dist must both have shape ({nq}, {int(k)})")
+    if len({Q.device, S.device, ids.device, dist.device}) != 1:
+        raise ValueError("Q, S, ids and dist must be on the same device")
     rc = load().ternary_knn_static(_ptr(Q), Q.shape[0], _ptr(S), S.shape[0], int(d), int(x),
                                    int(k), _ptr(ids), _ptr(dist), _ptr(status),
                                    _stream_handle(stream))
@@ -250,6 +263,23 @@ def rerank(Q: torch.Tensor, S: torch.Tensor, shortlist: torch.Tensor, k: int,
                        _ptr(ids), _ptr(scores), _ptr(status), _stream_handle(stream))
     _check(rc, "rerank")
     return ids, scores
+
+
+def test_stall_producer(path: int, fills: int):
+    """Testing support: the next launch of the tensor-core scan `path` stalls
+    its first CTA's copy producer after `fills` stage fills (evp.h)."""
+    _check(load().evp_test_stall_producer(int(path), int(fills)), "evp_test_stall_producer")
+
+
+def probe_tensor_rate(kind: int = 0, cta_pair: bool = False, n: int = 256,
+                      iters: int = 1 << 16, stream=None):
+    """evp_probe_tensor_rate: (TFLOP/s, SM clocks per instruction, ms) of
+    back-to-back tcgen05.mma (kind 0 = e4m3 f8f6f4, 1 = bf16 f16) on every SM."""
+    tf, cyc, ms = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().evp_probe_tensor_rate(int(kind), 1 if cta_pair else 0, int(n), int(iters),
+                                        ctypes.byref(tf), ctypes.byref(cyc), ctypes.byref(ms),
+                                        _stream_handle(stream)), "evp_probe_tensor_rate")
+    return tf.value, cyc.value, ms.value
 
 
 def timing_enable(on: bool = True):
