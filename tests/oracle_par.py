@@ -26,6 +26,22 @@ def encode(U: np.ndarray, x: int) -> np.ndarray:
     return out
 
 
+def pack(V: np.ndarray) -> np.ndarray:
+    """oracle.pack on row chunks in threads."""
+    n = V.shape[0]
+    if n < 4096:
+        return oracle.pack(V)
+    bounds = np.linspace(0, n, THREADS + 1).astype(np.int64)
+    parts = [None] * THREADS
+
+    def job(i):
+        parts[i] = oracle.pack(V[bounds[i]:bounds[i + 1]])
+
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        list(ex.map(job, range(THREADS)))
+    return np.concatenate(parts)
+
+
 def knn(Vq: np.ndarray, Vs: np.ndarray, k: int):
     nq = Vq.shape[0]
     ids = np.empty((nq, k), dtype=np.int64)

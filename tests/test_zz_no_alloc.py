@@ -1,9 +1,9 @@
 """ternary_knn_static -- the entry point that allocates nothing -- against
 the workspace-taking ternary_knn (popcount path), on two calls in a row.
 
-It is for callers that cannot allocate device memory (inside graph capture,
-allocator-free serving threads, plugins and plain C callers handed raw
-pointers); its scratch is a fixed array inside the library.  The file is
+It is for callers that cannot allocate device memory (serving threads that
+must stay out of the device allocator, plugins and plain C callers handed
+raw pointers); its scratch is a fixed array inside the library.  The file is
 named to be collected last."""
 import ctypes
 
@@ -49,3 +49,25 @@ def test_static_scratch_rejects_oversized_requests(evp_lib, dev):
     with pytest.raises(evp_lib.EvpError) as e:
         evp_lib.ternary_knn_static(Q, S, d, x, k, ids, dist)
     assert e.value.code == evp_lib.EVP_ERR_NO_MEMORY
+
+
+def test_static_binding_rejects_wrong_outputs(evp_lib, dev):
+    """The outputs are the caller's: a wrong shape, dtype or device is
+    refused on the host before anything is launched."""
+    d, x, k = 128, 40, 10
+    S = _codes(evp_lib, 2_000, d, x, 905, dev)
+    Q = _codes(evp_lib, 5, d, x, 906, dev)
+    ok_i = torch.empty((5, k), dtype=torch.int64, device=dev)
+    ok_d = torch.empty((5, k), dtype=torch.int32, device=dev)
+    bad = [
+        (torch.empty((5, k - 1), dtype=torch.int64, device=dev), ok_d),   # too small
+        (torch.empty((4, k), dtype=torch.int64, device=dev), ok_d),
+        (torch.empty((5, k), dtype=torch.int32, device=dev), ok_d),       # wrong dtype
+        (ok_i, torch.empty((5, k), dtype=torch.int64, device=dev)),
+        (torch.empty((5, k), dtype=torch.int64), ok_d),                   # host tensor
+    ]
+    for ids, dist in bad:
+        with pytest.raises(ValueError):
+            evp_lib.ternary_knn_static(Q, S, d, x, k, ids, dist)
+    evp_lib.ternary_knn_static(Q, S, d, x, k, ok_i, ok_d)
+    torch.cuda.synchronize()
