@@ -45,16 +45,60 @@ def parse():
     ap.add_argument("--centres", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-recall", action="store_true")
+    ap.add_argument("--no-probe", action="store_true",
+                    help="skip the tensor-core rate probe (roofline then uses 2 x bf16)")
     ap.add_argument("--path", type=int, default=0, help="0 auto, 1 popcount, 2 tensor core, 3 packed tensor core")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-form and served-form measurements")
-    ap.add_argument("--serve-seconds", type=float, default=4.0)
-    ap.add_argument("--serve-rate", type=float, default=150.0, help="requests/s (Poisson)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0)
+    ap.add_argument("--serve-rates", default="50,100,150,200,300,400",
+                    help="Poisson request rates (requests/s) of the served-form sweep")
     ap.add_argument("--recall-sweep", action="store_true",
                     help="instead of the benchmark: recall of the ternary scan against exact "
                          "float32 cosine kNN for several x (1M x 768 mixture by default)")
     ap.add_argument("--sweep-queries", type=int, default=2000)
     return ap.parse_args()
+
+
+def make_config(a, x, world):
+    """The workload description both arms print (identical dicts)."""
+    n, d, B = a.n, a.d, a.batch
+    W = (d + 63) // 64
+    return {"workload": f"{n}x{d} ternary kNN (Gaussian mixture, {a.centres} centres, "
+                        f"anisotropic), x={x}, batch {B} queries/step, shortlist "
+                        f"{a.shortlist} by Delta, rerank to k={a.k}",
+            "n": n, "d": d, "x": x, "batch": B, "shortlist": a.shortlist, "k": a.k,
+            "parallelism": f"replicas x{world}",
+            "l2": f"inputs larger than L2 (codes {n * 16 * W / 1e9:.2f} GB, floats "
+                  f"{n * d * 4 / 1e9:.1f} GB); no flush"}
+
+
+def measure_tensor_peak(evp, sampler_cls, local, seconds=1.0):
+    """Measured dense tensor-core rate (evp_probe_tensor_rate) for the
+    instruction shapes the scans issue, each run back to back for about
+    `seconds` with the SM clocks sampled meanwhile."""
+    out = {}
+    shapes = [("f8_pair_m256_n256", 0, True, 256), ("f8_m128_n256", 0, False, 256),
+              ("bf16_m128_n256", 1, False, 256), ("f8_m128_n64", 0, False, 64),
+              ("f8_m128_n16", 0, False, 16)]
+    for name, kind, pair, nn in shapes:
+        evp.probe_tensor_rate(kind, pair, nn, 1 << 12)          # warm-up
+        sampler = sampler_cls(local)
+        sampler.start()
+        t_end = time.perf_counter() + (seconds if nn == 256 else 0.25)
+        rates, cycles = [], []
+        while time.perf_counter() < t_end:
+            tf, cyc, _ = evp.probe_tensor_rate(kind, pair, nn, 1 << 16)
+            rates.append(tf)
+            cycles.append(cyc)
+        clk = sampler.stop()
+        m = 256 if pair else 128
+        kk = 32 if kind == 0 else 16
+        out[name] = {"tflops": float(np.median(rates)), "cycles_per_mma": float(np.median(cycles)),
+                     "flop_per_clk_per_sm": 2.0 * m * nn * kk / float(np.median(cycles)) / (2 if pair else 1),
+                     "launches": len(rates), "sm_mhz": clk.get("sm_mhz"),
+                     "reasons": clk.get("reasons")}
+    return out
 
 
 def load_peaks():
@@ -204,6 +248,13 @@ def cpu_oracle_sample(U_dev, Q_host, x, shortlist, k, n_total, n_rows=200_000, n
     t5 = time.perf_counter()
     scan_all = (t5 - t4) * scale / len(Vq_all)       # scan seconds per query, all cores
     per_query_all = ((t1 - t0) + (t3 - t2)) / n_q + scan_all
+    # the paper's float baseline ("Euclidean", Tables 4 and 5): exact float32
+    # brute force over the same rows, one thread
+    n_e = max(1, n_q // 4)
+    t6 = time.perf_counter()
+    oracle.l2_knn(Qs[:n_e], rows, k)
+    t7 = time.perf_counter()
+    euclid_per_query = (t7 - t6) * scale / n_e
     del torch
     return 1.0 / per_query, {
         "sample": f"{n_q} queries over the first {n_rows} database rows "
@@ -211,7 +262,11 @@ def cpu_oracle_sample(U_dev, Q_host, x, shortlist, k, n_total, n_rows=200_000, n
         "seconds": t3 - t0,
         "all_cores": {"value": 1.0 / per_query_all, "cores": cores,
                       "sample": f"{len(Vq_all)} concurrent query scans over the same rows, "
-                                "one per thread; encode and rerank as single-thread"}}
+                                "one per thread; encode and rerank as single-thread"},
+        "euclidean_fp32": {"value": 1.0 / euclid_per_query, "cores": 1,
+                           "sample": f"{n_e} queries, exact float32 squared-Euclidean brute "
+                                     f"force over the first {n_rows} rows (scaled x{scale:.0f}), "
+                                     f"top-{k}"}}
 
 
 def measure_batched(evp, synth, dev, seed_batches=64):
@@ -288,44 +343,87 @@ def measure_batched(evp, synth, dev, seed_batches=64):
                         "logU[1,8192] queries, k in {10,100}"}
 
 
-def measure_served(evp, synth, db, d, seconds, rate, dev):
-    """Served form: Poisson arrivals at `rate` requests/s for `seconds`,
-    request sizes round(logU[1, 1024]) queries, k in {10, 100}, shortlist
-    10 k (capped at 1024) reranked to k, continuous batching over 3 slots."""
-    import torch
-    rng = np.random.default_rng(20250602)
+def _request_stream(rate, seconds, seed):
+    rng = np.random.default_rng(seed)
     n_req = max(1, int(seconds * rate))
     arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
     sizes = np.clip(np.rint(np.exp(rng.uniform(0, np.log(1024), n_req))), 1, 1024).astype(int)
     ks = rng.choice([10, 100], n_req)
+    offs = rng.integers(0, 4096 - sizes + 1)
+    return arr, sizes, ks, offs
+
+
+def measure_served(evp, synth, db, d, seconds, rates, dev):
+    """Served form: for each Poisson rate, the same request stream (sizes
+    round(logU[1, 1024]) queries, k in {10, 100}, shortlist 10 k capped at
+    1024, reranked to k) run (a) through the continuous-batching server
+    (3 slots) and (b) as plain per-request evp_db_search_host calls in
+    arrival order on one stream; latency = completion - arrival."""
+    import torch
     pool = synth.mixture_torch(4096, d, n_centres=1024, anisotropic=True, stream=77,
                                device=dev).cpu().pin_memory()
+    out = []
     srv = evp.Server(db, max_batch_queries=4096, max_k=100, shortlist_factor=10, max_slots=3,
                      mem_budget_bytes=48 << 30)
-    # warm-up request of each class
-    for k in (10, 100):
+    for k in (10, 100):                                   # warm-up of each class
         srv.wait(srv.submit(pool[:64], k))
-    srv.reset_stats()
-    t0 = time.perf_counter()
-    rids = []
-    for i in range(n_req):
-        now = time.perf_counter() - t0
-        if arr[i] > now:
-            time.sleep(arr[i] - now)
-        off = int(rng.integers(0, 4096 - sizes[i] + 1))
-        rids.append(srv.submit(pool[off:off + sizes[i]], int(ks[i])))
-    for r in rids:
-        srv.wait(r, timeout_s=600)
-    wall = time.perf_counter() - t0
-    st = srv.stats()
+    ids_flat = torch.empty(1024 * 100, dtype=torch.int64).pin_memory()
+    sc_flat = torch.empty(1024 * 100, dtype=torch.float32).pin_memory()
+
+    def outs(nq, k):
+        return ids_flat[:nq * k].view(nq, k), sc_flat[:nq * k].view(nq, k)
+
+    stream = torch.cuda.Stream(dev)
+    ws = torch.empty(db.search_host_workspace_bytes(1024, 1000, 100), dtype=torch.uint8,
+                     device=dev)
+    for k in (10, 100):
+        db.search_host(pool[:64], min(10 * k, 1024), k, *outs(64, k), ws=ws, stream=stream)
+    stream.synchronize()
+    for rate in rates:
+        arr, sizes, ks, offs = _request_stream(rate, seconds, 20250602)
+        # (a) continuous batching
+        srv.reset_stats()
+        t0 = time.perf_counter()
+        rids = []
+        for i in range(len(arr)):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            rids.append(srv.submit(pool[offs[i]:offs[i] + sizes[i]], int(ks[i])))
+        for r in rids:
+            srv.wait(r, timeout_s=600)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        served = {"qps": int(sizes.sum()) / wall, "p50_ms": st["p50_us"] / 1e3,
+                  "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
+                  "batches": st["batches"], "wall_s": wall}
+        # (b) plain: one synchronous search per request, in arrival order
+        lat = []
+        t0 = time.perf_counter()
+        for i in range(len(arr)):
+            now = time.perf_counter() - t0
+            if arr[i] > now:
+                time.sleep(arr[i] - now)
+            k = int(ks[i])
+            nq = int(sizes[i])
+            db.search_host(pool[offs[i]:offs[i] + nq], min(10 * k, 1024), k, *outs(nq, k),
+                           ws=ws, stream=stream)
+            stream.synchronize()
+            lat.append(time.perf_counter() - t0 - arr[i])
+        wall_p = time.perf_counter() - t0
+        lat = np.array(lat) * 1e3
+        plain = {"qps": int(sizes.sum()) / wall_p, "p50_ms": float(np.percentile(lat, 50)),
+                 "p99_ms": float(np.percentile(lat, 99)), "max_ms": float(lat.max()),
+                 "wall_s": wall_p}
+        out.append({"rate_req_s": rate, "requests": len(arr), "queries": int(sizes.sum()),
+                    "offered_qps": int(sizes.sum()) / float(arr[-1]) if len(arr) > 1 else None,
+                    "continuous_batching": served, "plain_per_request": plain})
     slots = srv.slots
     srv.close()
-    return {"requests": n_req, "queries": int(sizes.sum()), "rate_req_s": rate,
-            "qps": int(sizes.sum()) / wall, "p50_ms": st["p50_us"] / 1e3,
-            "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3,
-            "batches": st["batches"], "slots": slots, "wall_s": wall,
+    return {"slots": slots, "sweep": out,
             "workload": "10Mx768 resident, Poisson arrivals, sizes logU[1,1024], "
-                        "k in {10,100}, shortlist 10k reranked"}
+                        "k in {10,100}, shortlist 10k reranked; each rate's stream run "
+                        "through the server and as plain per-request calls"}
 
 
 def main_reference(a):
@@ -356,8 +454,7 @@ def main_reference(a):
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1000.0 * a.batch / value, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int8 ternary / f64", "data": "synthetic",
-        "config": {"workload": f"{a.n}x{d} ternary kNN, x={x}, batch {a.batch}, "
-                               f"shortlist {a.shortlist}, k={a.k}"},
+        "config": make_config(a, x, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": "queries/s", "cores": 1, "kind": "oracle",
                          "sample": samp},
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
@@ -503,15 +600,13 @@ def main():
     torch.cuda.synchronize()
     evp.check_status(st, "warmup")
 
-    # ---- device-resident timing
+    # ---- device-resident timing (the library's kernel timing is off here)
     sampler = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
     time.sleep(0.3)
-    evp.timing_reset()
-    evp.timing_enable(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -519,20 +614,29 @@ def main():
         step(Qb[i % pool])
     e1.record(stream)
     torch.cuda.synchronize()
-    evp.timing_enable(False)
     clocks = sampler.stop()
     if world > 1:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    per_kernel = {name: evp.timing_read(name) for name in
-                  ("encode", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
-                   "scan_mma_packed", "final_merge", "rerank")}
     evp.check_status(st, "timed steps")
     # replicas: every rank searched its own B queries per step; the job's
     # throughput is all ranks' queries over the slowest rank's time
     total_q, ms = evp_dist.aggregate(B * a.steps, ms, device=dev)
     ms_per_step = ms / a.steps
     value = total_q / (ms / 1000.0)
+
+    # ---- per-kernel durations: the same steps again, with the library's
+    # CUDA events around each of its launches (on the launching stream)
+    evp.timing_reset()
+    evp.timing_enable(True)
+    for i in range(a.steps):
+        step(Qb[i % pool])
+    torch.cuda.synchronize()
+    evp.timing_enable(False)
+    per_kernel = {name: evp.timing_read(name) for name in
+                  ("encode", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
+                   "scan_mma_packed", "final_merge", "rerank")}
+    evp.check_status(st, "timed kernels")
 
     # ---- end to end through the API with host buffers (pinned)
     Qh = [q.cpu().pin_memory() for q in Qb]
@@ -564,43 +668,64 @@ def main():
     e2e_q, e2e_ms = evp_dist.aggregate(B * a.steps, e2e_ms, device=dev)
     e2e_value = e2e_q / (e2e_ms / 1000.0)
 
-    # ---- roofline of the dominant kernel
+    # ---- measured tensor-core peak (the probe), then the roofline of the
+    # dominant kernel
     hbm_peak, bf16_peak, peak_src = load_peaks()
+    tpeak = None if a.no_probe else measure_tensor_peak(evp, ClockSampler, local)
+    fp8_2x_bf16 = 2.0 * bf16_peak          # nominal fp8 : bf16 dense ratio 2 : 1
+    if tpeak:
+        fp8_peak = max(tpeak["f8_pair_m256_n256"]["tflops"], tpeak["f8_m128_n256"]["tflops"])
+        fp8_src = (f"fp8 dense measured by evp_probe_tensor_rate on every SM "
+                   f"({fp8_peak:.0f} TFLOP/s at {tpeak['f8_pair_m256_n256']['sm_mhz']} MHz); "
+                   f"2 x measured bf16 = {fp8_2x_bf16:.0f} beside it; HBM {hbm_peak} GB/s "
+                   f"({peak_src})")
+    else:
+        fp8_peak = fp8_2x_bf16
+        fp8_src = f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s ({peak_src}); HBM {hbm_peak} GB/s"
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     n_mma, mma_ms = per_kernel["scan_mma"]
     n_scan, scan_ms = per_kernel["scan_popc"]
     n_pk, pk_ms = per_kernel["scan_mma_packed"]
     if pk_ms > max(mma_ms, scan_ms):
         # packed tensor-core scan: one launch per <= 64 queries reads the
-        # packed codes (16 W bytes per row) once; 2 d flops per (query, row)
+        # packed codes (16 W bytes per row) once; 2 d flops per (query, row).
+        # Its instruction shape (M = 128, N <= 64) has a fixed cost per MMA,
+        # so its tensor ceiling is the probe's rate at that N.
         avg = pk_ms / max(1, n_pk)
         passes_per_step = (B + 63) // 64
+        qn = 16 if B <= 16 else 32 if B <= 32 else 64
         bytes_per_launch = float(n) * 16 * W
         flops = 2.0 * d * n * (B / passes_per_step)
-        fp8_peak = 2.0 * bf16_peak
         gbs = bytes_per_launch / (avg / 1e3) / 1e9
         tflops = flops / (avg / 1e3) / 1e12
         tensor_frac, hbm_frac = tflops / fp8_peak, gbs / hbm_peak
+        bound = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                 "frac": hbm_frac}
         if tensor_frac >= hbm_frac:
-            bound = {"bound": "tensor", "achieved": tflops, "peak": fp8_peak, "unit": "TFLOP/s",
-                     "frac": tensor_frac}
-        else:
-            bound = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": hbm_frac}
+            bound = {"bound": "tensor", "achieved": tflops, "peak": fp8_peak,
+                     "unit": "TFLOP/s", "frac": tensor_frac}
         roofline = {
             "kernel": "scan_mma_packed", **bound,
             "traffic": measured_traffic("scan_mma_packed", n, d, B, a.shortlist),
             "tensor_frac": tensor_frac, "hbm_frac": hbm_frac, "packed_gbs": gbs,
-            "peak_source": f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s; HBM {hbm_peak} GB/s ({peak_src})",
-            "launches": n_pk, "avg_ms": avg,
+            "peak_source": fp8_src, "launches": n_pk, "avg_ms": avg,
         }
+        if tpeak:
+            # MMA instructions per launch over the probe's instruction rate at this N
+            key = "f8_m128_n64" if qn == 64 else "f8_m128_n16"
+            cyc = tpeak[key]["cycles_per_mma"]
+            mmas = float((n + 127) // 128) * 2 * W       # 128-row tiles x K steps
+            mhz = clocks.get("sm_mhz") or 2070.0
+            floor_ms = mmas * cyc / sm_count / (mhz * 1e6) * 1e3
+            roofline["mma_instruction_floor_ms"] = floor_ms
+            roofline["frac_of_mma_instruction_floor"] = floor_ms / avg
+        dtype = "e4m3 x e4m3 -> f32 tensor-core scan (exact on -1/0/+1), f32 encode/rerank"
     elif mma_ms >= scan_ms:
         # tensor-core scan: algorithmic flops = 2 d per (query, row) pair; it
         # reads the database's e4m3 copy (Kp bytes per row) once per launch,
         # which binds instead for small batches
         avg = mma_ms / max(1, n_mma)
         flops = 2.0 * d * B * n * (a.steps / max(1, n_mma))
-        fp8_peak = 2.0 * bf16_peak   # nominal fp8 : bf16 dense ratio 2 : 1
         kp = (d + 127) // 128 * 128
         e4m3_bytes = float(n) * kp
         tflops = flops / (avg / 1e3) / 1e12
@@ -616,9 +741,10 @@ def main():
             "kernel": "scan_mma", **bound,
             "traffic": measured_traffic("scan_mma", n, d, B, a.shortlist),
             "tensor_frac": tensor_frac, "hbm_frac": hbm_frac, "e4m3_gbs": gbs,
-            "peak_source": f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s; HBM {hbm_peak} GB/s ({peak_src})",
-            "launches": n_mma, "avg_ms": avg,
+            "peak_2x_bf16": fp8_2x_bf16, "frac_vs_2x_bf16": tflops / fp8_2x_bf16,
+            "peak_source": fp8_src, "launches": n_mma, "avg_ms": avg,
         }
+        dtype = "e4m3 x e4m3 -> f32 tensor-core scan (exact on -1/0/+1), f32 encode/rerank"
     else:
         # popcount scan: one pass over the codes per <= 16 queries; per
         # (query, row) pair 4W 32-bit popcounts
@@ -644,41 +770,39 @@ def main():
             "peak_source": f"POPC 16/clk/SM (probe) x {sm_count} SMs x 2070 MHz; HBM {peak_src}",
             "launches": n_scan, "avg_ms": avg,
         }
+        dtype = "u64 bitplanes, popcount -> int32 Delta; f32 encode/rerank"
     kernels = {nm: {"launches": c, "total_ms": round(t, 3)} for nm, (c, t) in per_kernel.items()}
 
-    # ---- recall@10 against exact float32 cosine kNN (first 64 queries)
+    # ---- recall@10 against exact float32 cosine kNN, over the whole batch,
+    # for the bench's x and for the other x of the paper's table
     recall = None
     if not a.no_recall:
-        torch.backends.cuda.matmul.allow_tf32 = False
-        nrq = min(64, B)
-        Qr = Qb[0][:nrq]
+        Qr = Qb[0]
+        truth = exact_topk(Qr, U, k).cpu().numpy()
+        rec = lambda g, t: float(np.mean([len(set(a_[:k]) & set(b_[:k])) / k
+                                          for a_, b_ in zip(g, t)]))
         step(Qb[0])
         torch.cuda.synchronize()
-        best_s = torch.full((nrq, k), -float("inf"), device=dev)
-        best_i = torch.zeros((nrq, k), dtype=torch.int64, device=dev)
-        for c0 in range(0, n, 1 << 20):
-            s = Qr @ U[c0:c0 + (1 << 20)].T
-            v, i = torch.topk(s, k, dim=1)
-            cat_s = torch.cat([best_s, v], 1)
-            cat_i = torch.cat([best_i, i + c0], 1)
-            best_s, j = torch.topk(cat_s, k, dim=1)
-            best_i = torch.gather(cat_i, 1, j)
-        truth = best_i.cpu().numpy()
-        got_rr = rid[:nrq].cpu().numpy()
-        tq = evp.encode(Qr.contiguous(), x)
-        tern_ids, _ = db.knn(tq, k)
-        got_tern = tern_ids.cpu().numpy()
-        recall = {
-            "rerank_10_at_100": float(np.mean([len(set(a_) & set(b_)) / k
-                                               for a_, b_ in zip(got_rr, truth)])),
-            "ternary_10_at_10": float(np.mean([len(set(a_) & set(b_)) / k
-                                               for a_, b_ in zip(got_tern, truth)])),
-            "queries": nrq}
+        got_rr = rid.cpu().numpy()
+        tern_ids, _ = db.knn(evp.encode(Qr, x), k)
+        recall = {"queries": B, "x": x, "rerank_10_at_100": rec(got_rr, truth),
+                  "ternary_10_at_10": rec(tern_ids.cpu().numpy(), truth), "per_x": {}}
+        for xx in (64, 256, 384, x):
+            Tx = evp.encode(U, xx)
+            dbx = evp.Database(Tx, U, d, xx)
+            r_ids, _ = dbx.search(Qr, n_sl, k)
+            t_ids, _ = dbx.knn(evp.encode(Qr, xx), k)
+            recall["per_x"][str(xx)] = {"rerank_10_at_100": rec(r_ids.cpu().numpy(), truth),
+                                        "ternary_10_at_10": rec(t_ids.cpu().numpy(), truth)}
+            dbx.close()
+            del Tx, dbx
+            torch.cuda.empty_cache()
 
     # ---- batched and served forms (rank 0, N = 1)
     forms = None
     if not a.no_forms and world == 1:
-        served = measure_served(evp, synth, db, d, a.serve_seconds, a.serve_rate, dev)
+        rates = [float(r) for r in a.serve_rates.split(",") if r]
+        served = measure_served(evp, synth, db, d, a.serve_seconds, rates, dev)
         batched = measure_batched(evp, synth, dev)
         forms = {"batched": batched, "served": served}
 
@@ -687,24 +811,21 @@ def main():
     if not a.no_cpu_baseline and world == 1:
         v, info = cpu_oracle_sample(U, Qall[:64].cpu().numpy(), x, n_sl, k, n)
         cpu = {"value": v, "unit": "queries/s", "cores": 1, "kind": "oracle",
-               "sample": info["sample"], "all_cores": info["all_cores"]}
+               "sample": info["sample"], "all_cores": info["all_cores"],
+               "euclidean_fp32": info["euclidean_fp32"]}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_per_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "u64 bitplanes / int32 Delta / f32 rerank", "data": "synthetic",
-            "config": {"workload": f"{n}x{d} ternary kNN (Gaussian mixture, {a.centres} centres, "
-                                   f"anisotropic), x={x}, batch {B} queries/step, shortlist "
-                                   f"{n_sl} by Delta, rerank to k={k}",
-                       "n": n, "d": d, "x": x, "batch": B, "shortlist": n_sl, "k": k,
-                       "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (codes 1.92 GB, floats 30.7 GB); no flush"},
+            "dtype": dtype, "data": "synthetic",
+            "config": make_config(a, x, world),
             "scanned_gbs_logical": B * n * 16 * W / (ms_per_step / 1e3) / 1e9,
             "db_encode": {"rows": n, "ms": db_encode_ms,
                           "gbs": n * (4 * d + 16 * W) / (db_encode_ms / 1e3) / 1e9},
             "roofline": roofline,
+            "tensor_peak_probe": tpeak,
             "kernels": kernels,
             "recall_at_10": recall,
             "forms": forms,
