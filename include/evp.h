@@ -142,6 +142,45 @@ int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns
                     void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Single-operand translation (Sec. 6): the database is mapped to EVP
+ * vertices, the query keeps its values.  Here the query is held as int8, so
+ * that every score is an exact integer and results are reproducible bit for
+ * bit (the paper fixes no precision for the untranslated operand; int8
+ * keeps the recall of float queries on this build's synthetic data).
+ *
+ * evp_quantize_i8: per-query symmetric int8.  m = max_i |q_i|, scale =
+ * 127 / m in float32, q8_i = q_i * scale rounded to the nearest integer,
+ * ties to even (IEEE float32 arithmetic throughout); m = 0 gives zeros.
+ *   Q      [nq][d] float32, device.     Q8  [nq][d] int8 output, device.
+ *   dev_status receives EVP_ERR_NONFINITE for a NaN or infinite element
+ *   (that row is then all zero).
+ * Returns EVP_OK, EVP_ERR_INVALID or EVP_ERR_CUDA.
+ *
+ * ternary_knn_i8q: exhaustive search of Sec. 5.3 with the masked-addition
+ * score of Sec. 5.1.2 -- score(q, s) = sum of q8_i where s_i = +1 minus
+ * the sum where s_i = -1 (= <q8, s>, no multiplication needed) -- the k
+ * rows with the largest score per query, equal scores by lower row index.
+ *   Q8     [nq][d] int8 queries, device.
+ *   S      [ns][2W] packed database codes (as for ternary_knn), 16-byte
+ *          aligned; every code has x non-zeros.
+ *   ids    [nq][k] int64 output; score [nq][k] int32 output (descending).
+ *   ws     workspace of ternary_knn_i8q_workspace(...) bytes (0 means the
+ *          shape is not supported), 256-byte aligned.
+ * Runs on the tensor cores: database tiles unpacked on chip (as
+ * EVP_PATH_MMA_PACKED) against each query split exactly as 16 hi + lo with
+ * e4m3 parts, passes of up to 32 queries.  Limits as EVP_PATH_MMA_PACKED:
+ * d <= 768 with ceil(d/64) even, k <= 256 (else EVP_ERR_UNSUPPORTED).
+ * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_UNSUPPORTED, EVP_ERR_NO_MEMORY
+ * or EVP_ERR_CUDA; dev_status may receive EVP_ERR_TIMEOUT.
+ * ------------------------------------------------------------------- */
+int32_t evp_quantize_i8(const float* Q, int64_t nq, int32_t d, int8_t* Q8, int32_t* dev_status,
+                        void* stream);
+size_t ternary_knn_i8q_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k);
+int32_t ternary_knn_i8q(const int8_t* Q8, int64_t nq, const uint64_t* S, int64_t ns, int32_t d,
+                        int32_t x, int32_t k, int64_t* ids, int32_t* score, void* ws,
+                        size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
  * ternary_knn_static -- ternary_knn (popcount path) that allocates
  * nothing.  The paper has no counterpart; this exists for callers that
  * cannot allocate device memory: serving threads that must never enter the
@@ -447,7 +486,8 @@ int32_t evp_server_destroy(evp_server_t s);
  * on its stream around each launch of the library's kernels; (0) stops
  * recording.  evp_timing_read synchronises on the recorded events and
  * returns, for the kernel family `name` ("encode", "scan_init",
- * "scan_popc", "unpack_fp8", "scan_mma", "final_merge", "pack_lists", "rerank"), the number of launches and their total
+ * "scan_popc", "unpack_fp8", "scan_mma", "scan_mma_packed", "scan_i8q", "quantize",
+ * "final_merge", "pack_lists", "rerank"), the number of launches and their total
  * duration in milliseconds since the last evp_timing_reset.  Returns
  * EVP_OK, EVP_ERR_INVALID (null outputs) or EVP_ERR_CUDA.  Enabling adds
  * two event records per launch; leave it off outside measurements.
@@ -467,7 +507,10 @@ int32_t evp_timing_read(const char* name, int64_t* launches, double* total_ms);
  * thread, on operands resident in shared memory that hold +1, -1 and 0 in
  * equal shares (the values the scans contract).  cta_pair = 0: one CTA per
  * SM, M = 128; cta_pair = 1: CTA pairs (cta_group::2), M = 256.  n is a
- * multiple of 16 in [16, 256]; 1 <= iters <= 2^26.  Synchronous: the launch
+ * multiple of 16 in [16, 256]; 1 <= iters <= 2^26.  kind | 0x100 fills
+ * the operands with zeros instead, kind | 0x200 (e4m3 only) with random
+ * finite bytes, to show whether the rate depends on the values.
+ * Synchronous: the launch
  * is timed with CUDA events on `stream`.  Outputs: *tflops =
  * 2 M n K iters x instruction issuers / elapsed time; *cycles_per_mma =
  * SM clocks per instruction on the issuing thread (averaged over SMs);

@@ -68,7 +68,7 @@ __device__ __forceinline__ void pr_mma(int kind, uint32_t d, uint64_t a, uint64_
 
 template <int CG>
 __global__ void __launch_bounds__(PR_THREADS, 1)
-probe_mma_kernel(int kind, int n, int64_t iters, uint32_t idesc, int64_t* cycles,
+probe_mma_kernel(int kind, int fill, int n, int64_t iters, uint32_t idesc, int64_t* cycles,
                  int32_t* status) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
@@ -80,9 +80,16 @@ probe_mma_kernel(int kind, int n, int64_t iters, uint32_t idesc, int64_t* cycles
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t rank = CG == 2 ? pr_cluster_rank() : 0u;
 
-    // operands: +1 / -1 / 0 in equal shares (a fixed hash of the position)
+    // operands: +1 / -1 / 0 in equal shares (a fixed hash of the position),
+    // or all zero (fill = 1) or random bytes (fill = 2, e4m3 only)
     const int bytes = PR_A_BYTES + PR_B_BYTES;
     for (int i = tid; i < bytes / 2; i += PR_THREADS) {
+        if (fill != 0) {
+            const uint32_t h = ((uint32_t)i * 2654435761u + blockIdx.x * 40503u) >> 9;
+            uint16_t w = fill == 1 ? 0 : (uint16_t)(h & 0x7777u);  // finite e4m3 bytes
+            reinterpret_cast<uint16_t*>(smem)[i] = w;
+            continue;
+        }
         const uint32_t h = (uint32_t)i * 2654435761u + blockIdx.x * 40503u;
         const uint32_t c0 = (h >> 7) % 3u, c1 = (h >> 17) % 3u;
         uint16_t v;
@@ -173,7 +180,9 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
                               double* tflops, double* cycles_per_mma, double* ms, void* stream) {
     using namespace evp;
     const int cg = cta_pair ? 2 : 1;
-    if ((kind != 0 && kind != 1) || n < 16 || n > 256 || n % 16 != 0 || iters < 1 ||
+    const int fill = (kind >> 8) & 3;  // operand values (see evp.h)
+    kind &= 0xff;
+    if ((kind != 0 && kind != 1) || fill == 3 || (fill == 2 && kind != 0) || n < 16 || n > 256 || n % 16 != 0 || iters < 1 ||
         iters > (int64_t(1) << 26) || !tflops || !cycles_per_mma || !ms)
         return EVP_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -202,8 +211,8 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
                                    PR_SMEM_LAUNCH);
         if (err == cudaSuccess) {
             cudaEventRecord(e0, s);
-            probe_mma_kernel<1><<<workers, PR_THREADS, PR_SMEM_LAUNCH, s>>>(kind, n, iters, idesc,
-                                                                            cycles, status);
+            probe_mma_kernel<1><<<workers, PR_THREADS, PR_SMEM_LAUNCH, s>>>(kind, fill, n, iters,
+                                                                            idesc, cycles, status);
             err = cudaGetLastError();
             cudaEventRecord(e1, s);
         }
@@ -224,8 +233,8 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             cudaEventRecord(e0, s);
-            err = cudaLaunchKernelEx(&cfg, probe_mma_kernel<2>, kind, n, iters, idesc, cycles,
-                                     status);
+            err = cudaLaunchKernelEx(&cfg, probe_mma_kernel<2>, kind, fill, n, iters, idesc,
+                                     cycles, status);
             cudaEventRecord(e1, s);
         }
     }
