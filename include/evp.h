@@ -181,6 +181,37 @@ int32_t ternary_knn_i8q(const int8_t* Q8, int64_t nq, const uint64_t* S, int64_t
                         size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* ---------------------------------------------------------------------
+ * Sparse codes for small x (Sec. 6, "different EVPs": fewer non-zeros are
+ * less accurate but faster).  A sparse code lists the x non-zero
+ * dimensions of a vertex in ascending order, one uint16 each: bits 0-14 the
+ * dimension, bit 15 set where the element is -1; [n][x] row-major.  At
+ * x = 64, d = 768 it is 128 bytes per row against 192 for the bitplanes.
+ *
+ * evp_pack_sparse: packed bitplane codes T [n][2W] -> E [n][x] (device).
+ * A row with other than x non-zeros gets EVP_ERR_RANGE in dev_status (its
+ * first min(count, x) entries are written, the rest 0).  Returns EVP_OK,
+ * EVP_ERR_INVALID (d > 32768 among others) or EVP_ERR_CUDA.
+ *
+ * ternary_knn_sparse: exhaustive kNN (Sec. 5.3) of packed ternary queries Q
+ * [nq][2W] over a sparse database E [ns][x] (16-byte aligned): for each
+ * query the k rows with the smallest (Delta, row), Delta = ||q - s||^2 --
+ * the same results as ternary_knn over the bitplane form of the same codes.
+ * Delta is computed by masked addition (Sec. 5.1.2): per database row, one
+ * table lookup per non-zero.  Queries are scanned in passes of 4.  Needs
+ * 8 <= x <= 120 with x a multiple of 8, d <= 1024 and k <= 256 (else
+ * EVP_ERR_UNSUPPORTED; ternary_knn_sparse_workspace then returns 0).
+ * Workspace: ternary_knn_sparse_workspace(...) bytes, 256-byte aligned.
+ * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_UNSUPPORTED, EVP_ERR_NO_MEMORY or
+ * EVP_ERR_CUDA.
+ * ------------------------------------------------------------------- */
+int32_t evp_pack_sparse(const uint64_t* T, int64_t n, int32_t d, int32_t x, uint16_t* E,
+                        int32_t* dev_status, void* stream);
+size_t ternary_knn_sparse_workspace(int64_t nq, int64_t ns, int32_t d, int32_t x, int32_t k);
+int32_t ternary_knn_sparse(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t ns,
+                           int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist, void* ws,
+                           size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* ---------------------------------------------------------------------
  * ternary_knn_static -- ternary_knn (popcount path) that allocates
  * nothing.  The paper has no counterpart; this exists for callers that
  * cannot allocate device memory: serving threads that must never enter the
@@ -487,7 +518,8 @@ int32_t evp_server_destroy(evp_server_t s);
  * recording.  evp_timing_read synchronises on the recorded events and
  * returns, for the kernel family `name` ("encode", "scan_init",
  * "scan_popc", "unpack_fp8", "scan_mma", "scan_mma_packed", "scan_i8q", "quantize",
- * "final_merge", "pack_lists", "rerank"), the number of launches and their total
+ * "scan_sparse", "pack_sparse", "final_merge", "pack_lists", "rerank"), the number
+ * of launches and their total
  * duration in milliseconds since the last evp_timing_reset.  Returns
  * EVP_OK, EVP_ERR_INVALID (null outputs) or EVP_ERR_CUDA.  Enabling adds
  * two event records per launch; leave it off outside measurements.

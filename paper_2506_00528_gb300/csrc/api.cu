@@ -226,6 +226,64 @@ int32_t ternary_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns
                             EVP_PATH_AUTO);
 }
 
+int32_t evp_quantize_i8(const float* Q, int64_t nq, int32_t d, int8_t* Q8, int32_t* dev_status,
+                        void* stream) {
+    if (nq < 0 || d < 1) return EVP_ERR_INVALID;
+    if (nq == 0) return EVP_OK;
+    if (!Q || !Q8) return EVP_ERR_INVALID;
+    const cudaError_t e = launch_quantize_i8(Q, nq, d, Q8, dev_status,
+                                             static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+int32_t evp_pack_sparse(const uint64_t* T, int64_t n, int32_t d, int32_t x, uint16_t* E,
+                        int32_t* dev_status, void* stream) {
+    if (n < 0 || d < 1 || d > 32768 || x < 1 || x > d) return EVP_ERR_INVALID;
+    if (n == 0) return EVP_OK;
+    if (!T || !E) return EVP_ERR_INVALID;
+    const cudaError_t e = launch_pack_sparse(T, n, d, x, E, dev_status,
+                                             static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
+}
+
+size_t ternary_knn_sparse_workspace(int64_t nq, int64_t ns, int32_t d, int32_t x, int32_t k) {
+    if (nq < 0 || ns < 1 || !evp::sparse_supported(d, x, k)) return 0;
+    return evp::sparse_workspace(nq, ns, d, k);
+}
+
+int32_t ternary_knn_sparse(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t ns,
+                           int32_t d, int32_t x, int32_t k, int64_t* ids, int32_t* dist, void* ws,
+                           size_t ws_bytes, int32_t* dev_status, void* stream) {
+    if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
+        (int64_t)k > ns)
+        return EVP_ERR_INVALID;
+    if (!evp::sparse_supported(d, x, k)) return EVP_ERR_UNSUPPORTED;
+    if (nq == 0) return EVP_OK;
+    if (!Q || !E || !ids || !dist || !ws || (reinterpret_cast<uintptr_t>(E) & 15) != 0)
+        return EVP_ERR_INVALID;
+    return evp::run_sparse_knn(Q, nq, E, ns, d, x, k, ids, dist, ws, ws_bytes, dev_status,
+                               static_cast<cudaStream_t>(stream));
+}
+
+size_t ternary_knn_i8q_workspace(int64_t nq, int64_t ns, int32_t d, int32_t k) {
+    if (nq < 0 || ns < 1 || d < 1 || k < 1 || !evp::mma_packed_supported(ns, d, k)) return 0;
+    return evp::mma_packed_workspace(ns, d, k);
+}
+
+int32_t ternary_knn_i8q(const int8_t* Q8, int64_t nq, const uint64_t* S, int64_t ns, int32_t d,
+                        int32_t x, int32_t k, int64_t* ids, int32_t* score, void* ws,
+                        size_t ws_bytes, int32_t* dev_status, void* stream) {
+    if (nq < 0 || ns < 1 || ns >= (int64_t(1) << 31) || d < 1 || x < 1 || x > d || k < 1 ||
+        (int64_t)k > ns)
+        return EVP_ERR_INVALID;
+    if (!evp::mma_packed_supported(ns, d, k)) return EVP_ERR_UNSUPPORTED;
+    if (nq == 0) return EVP_OK;
+    if (!Q8 || !S || !ids || !score || !ws || (reinterpret_cast<uintptr_t>(S) & 15) != 0)
+        return EVP_ERR_INVALID;
+    return evp::run_i8q_knn(Q8, nq, S, ns, d, x, k, ids, score, ws, ws_bytes, dev_status,
+                            static_cast<cudaStream_t>(stream));
+}
+
 size_t evp_merge_topk_workspace(int64_t nq, int32_t nlists, int32_t k) {
     if (nq <= 0 || nlists < 1 || k < 1) return 0;
     return merge_topk_workspace(nq, nlists, k);

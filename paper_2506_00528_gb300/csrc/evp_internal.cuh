@@ -268,11 +268,18 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
                      int32_t* status, cudaStream_t stream);
 
 // Per-query merge of per-(query, slice) sorted key lists ([nq][nslices][2][k]
-// with meta [nq][nslices] = (length, buffer)) into the k best.
+// with meta [nq][nslices] = (length, buffer)) into the k best.  Histogram
+// bins count Delta/2 (bin_shift < 0) or (key >> 32) >> bin_shift; the
+// output distance is key >> 32, or dist_bias - (key >> 32) when dist_bias
+// is not 0 (the score of the int8-query scan).
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
                            const uint32_t* hist, const uint32_t* minhalf, int hist_bins,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
-                           cudaStream_t stream);
+                           cudaStream_t stream, int bin_shift = -1, int dist_bias = 0);
+
+// int8 queries (the single-operand translation of Sec. 6).
+cudaError_t launch_quantize_i8(const float* Q, int64_t n, int d, int8_t* Q8, int32_t* status,
+                               cudaStream_t stream);
 
 size_t merge_topk_workspace(int64_t nq, int nlists, int k);
 int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int nlists, int k,
@@ -326,6 +333,23 @@ size_t mma_packed_workspace(int64_t ns, int d, int k);
 int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
                            int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                            int32_t* status, cudaStream_t stream);
+
+// int8-query scan (the single-operand translation of Sec. 6 with the
+// masked-addition score of Sec. 5.1.2) on the packed tensor-core pipeline:
+// same limits and workspace as the packed scan; score[q][j] is <q8, s>,
+// ids ordered by (score descending, row ascending).
+int32_t run_i8q_knn(const int8_t* Q8, int64_t nq, const uint64_t* S, int64_t ns, int d, int x,
+                    int k, int64_t* ids, int32_t* score, void* ws, size_t ws_bytes,
+                    int32_t* status, cudaStream_t stream);
+
+// Sparse small-x codes (Sec. 6): pack from bitplanes, and the scan.
+bool sparse_supported(int d, int x, int k);
+size_t sparse_workspace(int64_t nq, int64_t ns, int d, int k);
+cudaError_t launch_pack_sparse(const uint64_t* T, int64_t n, int d, int x, uint16_t* E,
+                               int32_t* status, cudaStream_t stream);
+int32_t run_sparse_knn(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t ns, int d,
+                       int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
+                       int32_t* status, cudaStream_t stream);
 
 // Path the automatic rule takes for nq queries (resident_copy: the
 // database's e4m3 copy is resident).

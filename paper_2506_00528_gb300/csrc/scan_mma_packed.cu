@@ -50,7 +50,10 @@
 // once), waits for the copies and MMAs it issued and frees TMEM.
 #include "evp_internal.cuh"
 
+#include <cuda_fp8.h>
+
 #include <algorithm>
+#include <type_traits>
 
 namespace evp {
 
@@ -99,6 +102,12 @@ struct PkArgs {
     int hist_bins;         // 2x + 1
     int32_t* status;
     int stall_fills;  // testing: CTA 0's producer stops after this many fills (-1: never)
+    // int8-query mode (MODE 1): the pass's queries [nqg][d], the score key
+    // bias - score (bias = 127 x >= every score) and the histogram bin shift
+    const int8_t* Q8;
+    int d;
+    int bias;
+    int hshift;
 };
 
 __host__ __device__ inline size_t pk_align(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -114,13 +123,14 @@ struct PkLayout {
 
 // Shared-memory carve-up (offsets from a 1024-byte aligned base; `total`
 // includes the alignment slack of the dynamic allocation).
-__host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn) {
+// mode 1 (int8 queries) stages two query operands and 64-bit candidates.
+__host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn, int mode = 0) {
     PkLayout L;
     L.stage_bytes = pk_align((size_t)PK_ROWS * (2 * W + 2) * 8, 1024);
     L.b_off = L.stage_bytes * stages;
     const size_t states = (size_t)PK_EPI_WARPS * (qn / 2);
-    L.cand_off = L.b_off + (size_t)(W / 2) * qn * 128;  // W/2 K-chunks of qn x 128 B
-    L.scratch_off = L.cand_off + states * PK_CAP * 4;    // one staged list per epilogue warp
+    L.cand_off = L.b_off + (size_t)(W / 2) * qn * 128 * (mode ? 2 : 1);  // W/2 K-chunks of qn x 128 B
+    L.scratch_off = L.cand_off + states * PK_CAP * (mode ? 8 : 4);  // one staged list per epilogue warp
     L.tau_off = L.scratch_off + (size_t)PK_EPI_WARPS * PK_STAGE_LIST_K * 8;
     L.thr_off = L.tau_off + states * 8;
     L.ub_off = L.thr_off + states * 4;
@@ -226,31 +236,37 @@ __device__ __forceinline__ void unpack_word(uint64_t p, uint64_t m, uint32_t* o)
     unpack_half((uint32_t)(nz >> 32), (uint32_t)(m >> 32), o + 8);
 }
 
-// Candidate key (Delta/2 << 20 | row - row0) -> list key (Delta << 32 | row).
-__device__ __forceinline__ uint64_t pk_key64(uint32_t c, int64_t row0) {
-    return ((uint64_t)(2u * (c >> PK_LOCAL_BITS)) << 32) |
-           (uint64_t)(row0 + (int64_t)(c & ((1u << PK_LOCAL_BITS) - 1u)));
+// Candidate key -> list key.  Mode 0: (Delta/2 << 20 | row - row0), a
+// uint32, -> (Delta << 32 | row).  Mode 1: (score key << 20 | row - row0), a
+// uint64, -> (score key << 32 | row).
+template <int MODE, typename CandT>
+__device__ __forceinline__ uint64_t pk_key64(CandT c, int64_t row0) {
+    const uint64_t v = (uint64_t)(c >> PK_LOCAL_BITS);
+    return ((MODE == 0 ? 2u * v : v) << 32) |
+           (uint64_t)(row0 + (int64_t)(c & (CandT)((1u << PK_LOCAL_BITS) - 1u)));
 }
 
-__device__ __forceinline__ int lower_bound_cand(const uint32_t* C, int n, uint64_t key,
+template <int MODE, typename CandT>
+__device__ __forceinline__ int lower_bound_cand(const CandT* C, int n, uint64_t key,
                                                 int64_t row0) {
     int lo = 0, hi = n;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        if (pk_key64(C[mid], row0) < key) lo = mid + 1;
+        if (pk_key64<MODE>(C[mid], row0) < key) lo = mid + 1;
         else hi = mid;
     }
     return lo;
 }
 
 // Ascending bitonic sort of buf[0, P) (P a power of two) by one warp.
-__device__ __forceinline__ void warp_sort_u32(uint32_t* buf, int P, int lane) {
+template <typename T>
+__device__ __forceinline__ void warp_sort(T* buf, int P, int lane) {
     for (int kk = 2; kk <= P; kk <<= 1) {
         for (int j = kk >> 1; j > 0; j >>= 1) {
             for (int i = lane; i < P; i += 32) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
-                    const uint32_t x0 = buf[i], x1 = buf[ixj];
+                    const T x0 = buf[i], x1 = buf[ixj];
                     if ((x0 > x1) == ((i & kk) == 0)) {
                         buf[i] = x1;
                         buf[ixj] = x0;
@@ -266,26 +282,44 @@ __device__ __forceinline__ void warp_sort_u32(uint32_t* buf, int P, int lane) {
 // row): D > thr admits exactly Delta <= Delta(tau) (the exact key test
 // follows on the rare candidates).  No threshold yet: -2^22, below every D
 // and small enough that D - thr stays exact in float32.
+// Mode 1: D = 2 score (even), and D > thr admits exactly the score keys
+// bias - score <= the key of tau.
 constexpr float PK_ADMIT_ALL = -4194304.0f;
-__device__ __forceinline__ float pk_thr(uint64_t tau, int x) {
+template <int MODE>
+__device__ __forceinline__ float pk_thr(uint64_t tau, int x, int bias) {
     if (tau == KEY_NONE) return PK_ADMIT_ALL;
-    return (float)(2 * x - (int)(tau >> 32)) - 0.5f;
+    if (MODE == 0) return (float)(2 * x - (int)(tau >> 32)) - 0.5f;
+    return (float)(2 * (bias - (int)(tau >> 32))) - 1.0f;
 }
 
-template <int QN>
+// List key bounding every key counted in histogram bins 0..T (the union
+// bound): bins are Delta/2 (mode 0) or score key >> hshift (mode 1).
+template <int MODE>
+__device__ __forceinline__ uint64_t pk_bin_key(uint32_t T, int hshift) {
+    if (MODE == 0) return (uint64_t)(2u * T + 1u) << 32;
+    return ((uint64_t)(T + 1u) << hshift) << 32;
+}
+
+// MODE 0: packed query codes (ternary), Delta keys.  MODE 1: int8 queries,
+// each split as q = 16 hi + lo with hi in [-8, 8] and lo in [-8, 7] (both
+// exact in e4m3, 16 hi too), contracted as two operands into the same
+// accumulator: D = 2 <q, s>, the masked-addition score of Sec. 5.1.2 times
+// two, exact in float32.
+template <int QN, int MODE>
 __global__ void __launch_bounds__(PK_THREADS, 1)
 scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a) {
+    using CandT = std::conditional_t<MODE == 0, uint32_t, uint64_t>;
     constexpr uint32_t IDESC = pk_idesc(QN);
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
     const int W = a.W, k = a.k, x = a.x, S = a.stages;
-    const PkLayout L = pk_layout(W, S, QN);
+    const PkLayout L = pk_layout(W, S, QN, MODE);
     uint8_t* stages = smem;
     uint8_t* qop = smem + L.b_off;  // query operand, W/2 chunks of QN x 128 B
     constexpr int QH = QN / 2;  // queries per epilogue warp
     constexpr int NSTATE = PK_EPI_WARPS * QH;
-    uint32_t* cand = reinterpret_cast<uint32_t*>(smem + L.cand_off);   // [NSTATE][PK_CAP]
+    CandT* cand = reinterpret_cast<CandT*>(smem + L.cand_off);         // [NSTATE][PK_CAP]
     uint64_t* scratch = reinterpret_cast<uint64_t*>(smem + L.scratch_off);
     uint64_t* tau = reinterpret_cast<uint64_t*>(smem + L.tau_off);     // [NSTATE] thresholds
     float* thr_s = reinterpret_cast<float*>(smem + L.thr_off);         // [NSTATE] on D
@@ -338,23 +372,42 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         for (int i = tid; i < QN * units_per_row; i += PK_THREADS) {
             const int n = i / units_per_row, ku = i - n * units_per_row;
             const int kb0 = ku * 16;
-            uint32_t o[4] = {0u, 0u, 0u, 0u};
+            uint32_t o[4] = {0u, 0u, 0u, 0u}, o2[4] = {0u, 0u, 0u, 0u};
             if (n < a.nqg) {
                 const int w = kb0 >> 6;
-                const uint64_t p = a.Q[(int64_t)n * 2 * W + w];
-                const uint64_t m = a.Q[(int64_t)n * 2 * W + W + w];
+                if constexpr (MODE == 0) {
+                    const uint64_t p = a.Q[(int64_t)n * 2 * W + w];
+                    const uint64_t m = a.Q[(int64_t)n * 2 * W + W + w];
 #pragma unroll
-                for (int e = 0; e < 16; ++e) {
-                    const int s = (kb0 & 63) + e;  // K position within the word
-                    const int bit = 32 * (s >> 5) + 8 * (s & 3) + ((s & 31) >> 2);
-                    const uint32_t byte = ((p >> bit) & 1u) ? 0x38u : (((m >> bit) & 1u) ? 0xB8u : 0u);
-                    o[e >> 2] |= byte << (8 * (e & 3));
+                    for (int e = 0; e < 16; ++e) {
+                        const int s = (kb0 & 63) + e;  // K position within the word
+                        const int bit = 32 * (s >> 5) + 8 * (s & 3) + ((s & 31) >> 2);
+                        const uint32_t byte =
+                            ((p >> bit) & 1u) ? 0x38u : (((m >> bit) & 1u) ? 0xB8u : 0u);
+                        o[e >> 2] |= byte << (8 * (e & 3));
+                    }
+                } else {
+                    const int8_t* q8 = a.Q8 + (int64_t)n * a.d;
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int s = (kb0 & 63) + e;  // K position within the word
+                        const int dim = 64 * w + 32 * (s >> 5) + 8 * (s & 3) + ((s & 31) >> 2);
+                        const int v = dim < a.d ? (int)q8[dim] : 0;
+                        const int hi = (v + 8) >> 4, lo = v - 16 * hi;
+                        const uint32_t bh = __nv_cvt_float_to_fp8((float)(16 * hi), __NV_SATFINITE, __NV_E4M3);
+                        const uint32_t bl = __nv_cvt_float_to_fp8((float)lo, __NV_SATFINITE, __NV_E4M3);
+                        o[e >> 2] |= bh << (8 * (e & 3));
+                        o2[e >> 2] |= bl << (8 * (e & 3));
+                    }
                 }
             }
             const int c = kb0 >> 7, uc = (kb0 & 127) >> 4;
             uint8_t* dst = qop + (size_t)c * QN * 128 + (n >> 3) * 1024 + (n & 7) * 128 +
                            ((uc ^ (n & 7)) << 4);
             *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+            if constexpr (MODE == 1)   // the lo operand follows the hi one
+                *reinterpret_cast<uint4*>(dst + (size_t)(W / 2) * QN * 128) =
+                    make_uint4(o2[0], o2[1], o2[2], o2[3]);
         }
         fence_proxy_async_smem();  // generic-proxy writes read by the tensor core
     }
@@ -425,6 +478,8 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             // field (16-byte units): chunk kk / 4 of QN x 128 B, 32 B per step;
             // all computed once, so that the loop issues little besides MMAs
             const uint64_t bdesc0 = sw128_desc(smem_u32(qop));
+            // mode 1: the lo operand's descriptor start address (16-byte units)
+            const uint64_t lo_off = (uint64_t)((W / 2) * QN * 128 / 16);
             uint64_t bd[2 * PK_W_MAX];
 #pragma unroll
             for (int kk = 0; kk < 2 * PK_W_MAX; ++kk)
@@ -442,9 +497,15 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                 const uint32_t dt = tmem_base + (uint32_t)(PK_D_COL0 + b * QN);
                 const uint32_t at = tmem_base + (uint32_t)(b * PK_A_COLS);
                 mma_f8_tmem_a(dt, at, bd[0], IDESC, 0u);
+                if constexpr (MODE == 1) mma_f8_tmem_a(dt, at, bd[0] + lo_off, IDESC, 1u);
 #pragma unroll
-                for (int kk = 1; kk < 2 * PK_W_MAX; ++kk)
-                    if (kk < ksteps) mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk], IDESC, 1u);
+                for (int kk = 1; kk < 2 * PK_W_MAX; ++kk) {
+                    if (kk < ksteps) {
+                        mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk], IDESC, 1u);
+                        if constexpr (MODE == 1)
+                            mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk] + lo_off, IDESC, 1u);
+                    }
+                }
                 mma_commit(&d_full[b]);  // one commit per tile: each drains the MMA pipe
             }
             if (!ok) give_up();
@@ -517,7 +578,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
         const int lslice = slice * PK_LISTS_PER_CTA + quad;  // this warp's list index
         const int nlists = nslices * PK_LISTS_PER_CTA;
-        uint32_t* candw = cand + e * QH * PK_CAP;
+        CandT* candw = cand + e * QH * PK_CAP;
         uint64_t* tauw = tau + e * QH;
         float* thrw = thr_s + e * QH;
         int* cntw = cnt + e * QH;
@@ -528,11 +589,11 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         // new threshold from the list's k-th key and the union bound
         auto merge = [&](int j, bool fin) {
             const int q = qbase + j, nc = cntw[j];
-            uint32_t* C = candw + j * PK_CAP;
+            CandT* C = candw + j * PK_CAP;
             const int P = next_pow2(nc);
-            for (int i = nc + lane; i < P; i += 32) C[i] = 0xFFFFFFFFu;
+            for (int i = nc + lane; i < P; i += 32) C[i] = ~(CandT)0;
             __syncwarp();
-            warp_sort_u32(C, P, lane);
+            warp_sort(C, P, lane);
             uint64_t* base = a.lists + ((int64_t)q * nlists + lslice) * 2 * k;
             const int c0 = curw[j], nL = lenw[j];
             const uint64_t* Lst = base + (int64_t)c0 * k;
@@ -546,11 +607,11 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             }
             for (int i = lane; i < nL; i += 32) {
                 const uint64_t key = Lst[i];
-                const int rr = i + lower_bound_cand(C, nc, key, row0);
+                const int rr = i + lower_bound_cand<MODE>(C, nc, key, row0);
                 if (rr < k) out[rr] = key;
             }
             for (int i = lane; i < nc; i += 32) {
-                const uint64_t key = pk_key64(C[i], row0);
+                const uint64_t key = pk_key64<MODE>(C[i], row0);
                 const int rr = i + lower_bound_u64(Lst, nL, key);
                 if (rr < k) out[rr] = key;
             }
@@ -559,7 +620,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             if (lane == 0) {
                 uint64_t t_new = nl == k ? out[k - 1] : KEY_NONE;
                 const uint32_t T = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
-                if (!fin && T != 0xFFFFFFFFu) t_new = min(t_new, (uint64_t)(2u * T + 1u) << 32);
+                if (!fin && T != 0xFFFFFFFFu) t_new = min(t_new, pk_bin_key<MODE>(T, a.hshift));
                 curw[j] = c0 ^ 1;
                 lenw[j] = nl;
                 cntw[j] = 0;
@@ -571,7 +632,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                     tq = min(tq, (uint64_t)old);
                 }
                 tauw[j] = tq;
-                if (q < a.nqg) thrw[j] = pk_thr(tq, x);
+                if (q < a.nqg) thrw[j] = pk_thr<MODE>(tq, x, a.bias);
             }
             __syncwarp();
         };
@@ -623,19 +684,29 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                 for (int j = 0; j < QH; ++j) {
                     if (!((any >> j) & 1u)) continue;
                     const int q = qbase + j;
-                    // Delta = 2x - D lies in [0, 4x] for codes with x non-zeros;
-                    // clamped so that other codes cannot index outside the histogram
+                    // mode 0: Delta = 2x - D lies in [0, 4x] for codes with x
+                    // non-zeros; mode 1: the score key bias - D/2 lies in
+                    // [0, 2 bias]; clamped so that other codes cannot index
+                    // outside the histogram
                     const float dq = __uint_as_float(v[j]) + thrw[j];
-                    const uint32_t delta = (uint32_t)min(max(2 * x - __float2int_rn(dq), 0), 4 * x);
+                    uint32_t kv, half;
+                    if constexpr (MODE == 0) {
+                        kv = (uint32_t)min(max(2 * x - __float2int_rn(dq), 0), 4 * x);
+                        half = kv >> 1;
+                    } else {
+                        kv = (uint32_t)min(max(a.bias - (__float2int_rn(dq) >> 1), 0), 2 * a.bias);
+                        half = kv >> a.hshift;
+                    }
                     bool c = (msk >> j) & 1u;
-                    if (c) c = (((uint64_t)delta << 32) | (uint64_t)row) < tauw[j];
+                    if (c) c = (((uint64_t)kv << 32) | (uint64_t)row) < tauw[j];
                     const uint32_t am = __ballot_sync(0xffffffffu, c);
                     if (!am) continue;
                     const int pos0 = cntw[j];
-                    const uint32_t half = delta >> 1;
                     if (c) {
                         const int rank = __popc(am & ((1u << lane) - 1u));
-                        candw[j * PK_CAP + pos0 + rank] = (half << PK_LOCAL_BITS) | (uint32_t)(row - row0);
+                        const CandT kc = MODE == 0 ? (CandT)half : (CandT)kv;
+                        candw[j * PK_CAP + pos0 + rank] =
+                            (kc << PK_LOCAL_BITS) | (CandT)(uint32_t)(row - row0);
                         // each row is appended at most once: count it for the union bound
                         atomicAdd(&a.hist[(int64_t)q * a.hist_bins + half], 1u);
                     }
@@ -662,9 +733,9 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                     const int q = qbase + lane;
                     uint64_t tq = min(tauw[lane], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[q]));
                     const uint32_t T = *reinterpret_cast<volatile uint32_t*>(&ub[q]);
-                    if (T != 0xFFFFFFFFu) tq = min(tq, (uint64_t)(2u * T + 1u) << 32);
+                    if (T != 0xFFFFFFFFu) tq = min(tq, pk_bin_key<MODE>(T, a.hshift));
                     tauw[lane] = tq;
-                    thrw[lane] = pk_thr(tq, x);
+                    thrw[lane] = pk_thr<MODE>(tq, x, a.bias);
                 }
                 __syncwarp();
             }
@@ -753,22 +824,26 @@ __global__ void pk_init_kernel(uint64_t* tau_global, uint32_t* hist, int hist_wo
     for (int i = threadIdx.x; i < hist_words; i += blockDim.x) hist[i] = 0u;
 }
 
-int pk_stages(int W, int qn) {
+int pk_stages(int W, int qn, int mode) {
     for (int s = PK_MAX_STAGES; s >= PK_MIN_STAGES; --s)
-        if (pk_layout(W, s, qn).total <= (size_t)PK_SMEM_LIMIT) return s;
+        if (pk_layout(W, s, qn, mode).total <= (size_t)PK_SMEM_LIMIT) return s;
     return 0;
 }
 
-template <int QN>
+template <int QN, int MODE>
 cudaError_t launch_pk(const CUtensorMap& tmap, const PkArgs& a, int nslices, cudaStream_t stream) {
-    const size_t smem = pk_layout(a.W, a.stages, QN).total;
-    cudaError_t e = cudaFuncSetAttribute(scan_mma_packed_kernel<QN>,
+    const size_t smem = pk_layout(a.W, a.stages, QN, MODE).total;
+    cudaError_t e = cudaFuncSetAttribute(scan_mma_packed_kernel<QN, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    TimedLaunch timer("scan_mma_packed", stream);
-    scan_mma_packed_kernel<QN><<<nslices, PK_THREADS, smem, stream>>>(tmap, a);
+    TimedLaunch timer(MODE == 0 ? "scan_mma_packed" : "scan_i8q", stream);
+    scan_mma_packed_kernel<QN, MODE><<<nslices, PK_THREADS, smem, stream>>>(tmap, a);
     return cudaGetLastError();
 }
+
+// Queries per pass of the int8-query mode: two query operands and 64-bit
+// candidates leave room for at most 32 in shared memory.
+constexpr int PK_I8Q_QN_MAX = 32;
 
 struct PkPlan {
     int nslices;
@@ -802,9 +877,14 @@ bool mma_packed_supported(int64_t ns, int d, int k) {
 
 size_t mma_packed_workspace(int64_t ns, int d, int k) { return plan_pk(ns, d, k).ws_bytes; }
 
-int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
-                           int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
-                           int32_t* status, cudaStream_t stream) {
+namespace {
+
+// Both modes: MODE 0 takes packed query codes Qp ([nq][2W] uint64), MODE 1
+// int8 queries ([nq][d]).
+template <int MODE>
+int32_t run_pk(const void* Qp, int64_t nq, const uint64_t* S, int64_t ns, int d, int x, int k,
+               int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes, int32_t* status,
+               cudaStream_t stream) {
     if (!mma_packed_supported(ns, d, k)) return EVP_ERR_UNSUPPORTED;
     const int W = (d + 63) / 64;
     const PkPlan p = plan_pk(ns, d, k);
@@ -829,6 +909,7 @@ int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int
     a.W = W;
     a.x = x;
     a.k = k;
+    a.d = d;
     a.pitch = pitch;
     a.ntiles = p.ntiles;
     a.tiles_per_slice = p.tiles_per_slice;
@@ -837,16 +918,22 @@ int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int
     a.hist = reinterpret_cast<uint32_t*>(w + p.list_bytes + p.meta_bytes);
     a.minhalf = reinterpret_cast<uint32_t*>(w + p.list_bytes + p.meta_bytes + p.hist_bytes - 256);
     a.tau_global = reinterpret_cast<uint64_t*>(w + p.list_bytes + p.meta_bytes + p.hist_bytes);
-    a.hist_bins = 2 * x + 1;
+    // mode 1: score keys 127 x - score in [0, 254 x], counted in bins of 2^7
+    // (at most 2x + 1 bins, the mode-0 histogram's size)
+    a.bias = 127 * x;
+    a.hshift = 7;
+    a.hist_bins = MODE == 0 ? 2 * x + 1 : ((2 * a.bias) >> a.hshift) + 1;
     a.status = status;
-    a.stall_fills = take_stall_packed();
+    a.stall_fills = MODE == 0 ? take_stall_packed() : -1;
 
-    for (int64_t q0 = 0; q0 < nq; q0 += PK_QN_MAX) {
-        const int nqg = (int)std::min<int64_t>(PK_QN_MAX, nq - q0);
+    const int qn_max = MODE == 0 ? PK_QN_MAX : PK_I8Q_QN_MAX;
+    for (int64_t q0 = 0; q0 < nq; q0 += qn_max) {
+        const int nqg = (int)std::min<int64_t>(qn_max, nq - q0);
         const int qn = nqg <= 16 ? 16 : nqg <= 32 ? 32 : 64;
-        a.Q = Q + q0 * 2 * W;
+        if (MODE == 0) a.Q = static_cast<const uint64_t*>(Qp) + q0 * 2 * W;
+        else a.Q8 = static_cast<const int8_t*>(Qp) + q0 * d;
         a.nqg = nqg;
-        a.stages = pk_stages(W, qn);
+        a.stages = pk_stages(W, qn, MODE);
         if (a.stages == 0) return EVP_ERR_UNSUPPORTED;
         {
             TimedLaunch timer("scan_init", stream);
@@ -854,16 +941,32 @@ int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int
                                                   a.minhalf);
         }
         cudaError_t e;
-        if (qn == 16) e = launch_pk<16>(tmap, a, p.nslices, stream);
-        else if (qn == 32) e = launch_pk<32>(tmap, a, p.nslices, stream);
-        else e = launch_pk<64>(tmap, a, p.nslices, stream);
+        if (qn == 16) e = launch_pk<16, MODE>(tmap, a, p.nslices, stream);
+        else if (qn == 32) e = launch_pk<32, MODE>(tmap, a, p.nslices, stream);
+        else if constexpr (MODE == 0) e = launch_pk<64, MODE>(tmap, a, p.nslices, stream);
+        else e = cudaErrorInvalidValue;
         if (e != cudaSuccess) return EVP_ERR_CUDA;
-        const int32_t rc = launch_final_merge(a.lists, a.meta, a.tau_global, a.hist, a.minhalf,
-                                              a.hist_bins, nqg, p.nslices * PK_LISTS_PER_CTA, k,
-                                              ids + q0 * k, dist + q0 * k, stream);
+        const int32_t rc = launch_final_merge(
+            a.lists, a.meta, a.tau_global, a.hist, a.minhalf, a.hist_bins, nqg,
+            p.nslices * PK_LISTS_PER_CTA, k, ids + q0 * k, dist + q0 * k, stream,
+            MODE == 0 ? -1 : a.hshift, MODE == 0 ? 0 : a.bias);
         if (rc != EVP_OK) return rc;
     }
     return EVP_OK;
+}
+
+}  // namespace
+
+int32_t run_mma_packed_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t ns, int d,
+                           int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
+                           int32_t* status, cudaStream_t stream) {
+    return run_pk<0>(Q, nq, S, ns, d, x, k, ids, dist, ws, ws_bytes, status, stream);
+}
+
+int32_t run_i8q_knn(const int8_t* Q8, int64_t nq, const uint64_t* S, int64_t ns, int d, int x,
+                    int k, int64_t* ids, int32_t* score, void* ws, size_t ws_bytes,
+                    int32_t* status, cudaStream_t stream) {
+    return run_pk<1>(Q8, nq, S, ns, d, x, k, ids, score, ws, ws_bytes, status, stream);
 }
 
 }  // namespace evp

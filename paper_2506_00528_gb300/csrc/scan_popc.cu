@@ -414,8 +414,8 @@ __global__ void __launch_bounds__(FM_THREADS)
 final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
                    const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
                    const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k,
-                   int key_bits, int stage_lists, int64_t* __restrict__ ids,
-                   int32_t* __restrict__ dist) {
+                   int key_bits, int stage_lists, int bin_shift, int dist_bias,
+                   int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int red[FM_THREADS / 32];
     __shared__ int total_s;
@@ -487,7 +487,10 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
             before += total;
             if (kth_bin != 0xFFFFFFFFu || before >= (uint32_t)k) break;
         }
-        if (kth_bin != 0xFFFFFFFFu) T = min(T, (uint64_t)(2u * kth_bin + 1u) << 32);
+        // histogram bins are Delta/2 (bin_shift < 0) or (key >> 32) >> bin_shift
+        if (kth_bin != 0xFFFFFFFFu)
+            T = min(T, bin_shift < 0 ? (uint64_t)(2u * kth_bin + 1u) << 32
+                                     : ((uint64_t)(kth_bin + 1u) << bin_shift) << 32);
     }
     int m = T != KEY_NONE ? count_le(T) : FM_GATHER + 1;
     if (m < k || m > FM_GATHER) {
@@ -552,7 +555,8 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
     for (int j = tid; j < k; j += FM_THREADS) {
         const uint64_t key = j < n ? out[j] : KEY_NONE;
         ids[q * k + j] = key == KEY_NONE ? -1 : (int64_t)(key & 0xffffffffull);
-        dist[q * k + j] = key == KEY_NONE ? -1 : (int32_t)(key >> 32);
+        dist[q * k + j] = key == KEY_NONE ? -1
+                          : dist_bias ? dist_bias - (int32_t)(key >> 32) : (int32_t)(key >> 32);
     }
 }
 
@@ -625,7 +629,7 @@ __global__ void pack_lists_kernel(const int64_t* __restrict__ ids, const int32_t
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
                            const uint32_t* hist, const uint32_t* minhalf, int hist_bins,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
-                           cudaStream_t stream) {
+                           cudaStream_t stream, int bin_shift, int dist_bias) {
     if (nq <= 0) return EVP_OK;
     if (nslices > FM_MAX_SLICES) return EVP_ERR_UNSUPPORTED;
     const size_t list_bytes = (size_t)nslices * k * 8;
@@ -634,11 +638,13 @@ int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uin
     if (cudaFuncSetAttribute(final_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4 + FM_STAGE_BYTES) != cudaSuccess)
         return EVP_ERR_CUDA;
-    // keys are (Delta << 32 | row) with Delta <= 4 * EVP_MAX_D_SCAN
-    const int key_bits = 32 + 13;
+    // keys are (Delta << 32 | row) with Delta <= 4 * EVP_MAX_D_SCAN, or
+    // (bias - score) << 32 | row with the score key below 2^18
+    const int key_bits = 32 + (bin_shift < 0 ? 13 : 18);
     TimedLaunch timer("final_merge", stream);
     final_merge_kernel<<<(unsigned)nq, FM_THREADS, smem, stream>>>(
-        lists, meta, tau, hist, minhalf, hist_bins, nslices, k, key_bits, stage, ids, dist);
+        lists, meta, tau, hist, minhalf, hist_bins, nslices, k, key_bits, stage, bin_shift,
+        dist_bias, ids, dist);
     return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 

@@ -53,6 +53,12 @@ SIGNATURES = {
     "ternary_knn_path": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _sz, _p, _p,
                                 _i32]),
     "ternary_knn_static": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _p]),
+    "evp_quantize_i8": (_i32, [_p, _i64, _i32, _p, _p, _p]),
+    "evp_pack_sparse": (_i32, [_p, _i64, _i32, _i32, _p, _p, _p]),
+    "ternary_knn_sparse_workspace": (_sz, [_i64, _i64, _i32, _i32, _i32]),
+    "ternary_knn_sparse": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
+    "ternary_knn_i8q_workspace": (_sz, [_i64, _i64, _i32, _i32]),
+    "ternary_knn_i8q": (_i32, [_p, _i64, _p, _i64, _i32, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
     "rerank": (_i32, [_p, _i64, _p, _i64, _i32, _p, _i32, _i32, _p, _p, _p, _p]),
     "evp_merge_topk_workspace": (_sz, [_i64, _i32, _i32]),
     "evp_merge_topk": (_i32, [_p, _p, _i64, _i32, _i32, _p, _p, _p, _sz, _p, _p]),
@@ -205,6 +211,91 @@ def ternary_knn(Q: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
                                      _ptr(ids), _ptr(dist), _ptr(ws), ws.numel(), _ptr(status),
                                      _stream_handle(stream), int(path))
     _check(rc, "ternary_knn")
+    return ids, dist
+
+
+def quantize_i8(Q: torch.Tensor, out: torch.Tensor | None = None,
+                status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """evp_quantize_i8: float32 [nq, d] -> int8 [nq, d] (symmetric per query)."""
+    _req(Q, torch.float32, "Q")
+    nq, d = Q.shape
+    if out is None:
+        out = torch.empty((nq, d), dtype=torch.int8, device=Q.device)
+    _req(out, torch.int8, "out")
+    if tuple(out.shape) != (nq, d):
+        raise ValueError("out must have the shape of Q")
+    _check(load().evp_quantize_i8(_ptr(Q), nq, d, _ptr(out), _ptr(status), _stream_handle(stream)),
+           "evp_quantize_i8")
+    return out
+
+
+def ternary_knn_i8q(Q8: torch.Tensor, S: torch.Tensor, d: int, x: int, k: int,
+                    ids: torch.Tensor | None = None, score: torch.Tensor | None = None,
+                    ws: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                    stream=None):
+    """ternary_knn_i8q: int8 queries [nq, d], packed S [ns, 2W] -> ids int64,
+    score int32 [nq, k] (largest masked-addition score first)."""
+    _req(Q8, torch.int8, "Q8")
+    _req(S, torch.int64, "S")
+    nq, ns = Q8.shape[0], S.shape[0]
+    if Q8.shape[1] != d or S.shape[1] != 2 * words(d):
+        raise ValueError("Q8 must be [nq, d] and S [ns, 2W]")
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q8.device)
+    if score is None:
+        score = torch.empty((nq, k), dtype=torch.int32, device=Q8.device)
+    need = int(load().ternary_knn_i8q_workspace(nq, ns, int(d), int(k)))
+    if need == 0:
+        raise EvpError(EVP_ERR_UNSUPPORTED, "ternary_knn_i8q")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=Q8.device)
+    _check(load().ternary_knn_i8q(_ptr(Q8), nq, _ptr(S), ns, int(d), int(x), int(k), _ptr(ids),
+                                  _ptr(score), _ptr(ws), ws.numel(), _ptr(status),
+                                  _stream_handle(stream)), "ternary_knn_i8q")
+    return ids, score
+
+
+def pack_sparse(T: torch.Tensor, d: int, x: int, out: torch.Tensor | None = None,
+                status: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """evp_pack_sparse: packed codes [n, 2W] -> sparse codes int16 [n, x]
+    (the uint16 entries' bits: dimension | 0x8000 for -1)."""
+    _req(T, torch.int64, "T")
+    n = T.shape[0]
+    if T.shape[1] != 2 * words(d):
+        raise ValueError("T must be [n, 2W] packed codes for this d")
+    if out is None:
+        out = torch.empty((n, int(x)), dtype=torch.int16, device=T.device)
+    _req(out, torch.int16, "out")
+    if tuple(out.shape) != (n, int(x)):
+        raise ValueError("out must be [n, x]")
+    _check(load().evp_pack_sparse(_ptr(T), n, int(d), int(x), _ptr(out), _ptr(status),
+                                  _stream_handle(stream)), "evp_pack_sparse")
+    return out
+
+
+def ternary_knn_sparse(Q: torch.Tensor, E: torch.Tensor, d: int, x: int, k: int,
+                       ids: torch.Tensor | None = None, dist: torch.Tensor | None = None,
+                       ws: torch.Tensor | None = None, status: torch.Tensor | None = None,
+                       stream=None):
+    """ternary_knn_sparse: packed queries [nq, 2W], sparse database [ns, x]
+    -> ids int64, dist int32 [nq, k] (the results of ternary_knn)."""
+    _req(Q, torch.int64, "Q")
+    _req(E, torch.int16, "E")
+    nq, ns = Q.shape[0], E.shape[0]
+    if Q.shape[1] != 2 * words(d) or E.shape[1] != x:
+        raise ValueError("Q must be [nq, 2W] and E [ns, x]")
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int64, device=Q.device)
+    if dist is None:
+        dist = torch.empty((nq, k), dtype=torch.int32, device=Q.device)
+    need = int(load().ternary_knn_sparse_workspace(nq, ns, int(d), int(x), int(k)))
+    if need == 0:
+        raise EvpError(EVP_ERR_UNSUPPORTED, "ternary_knn_sparse")
+    if ws is None or ws.numel() < need:
+        ws = torch.empty(need, dtype=torch.uint8, device=Q.device)
+    _check(load().ternary_knn_sparse(_ptr(Q), nq, _ptr(E), ns, int(d), int(x), int(k), _ptr(ids),
+                                     _ptr(dist), _ptr(ws), ws.numel(), _ptr(status),
+                                     _stream_handle(stream)), "ternary_knn_sparse")
     return ids, dist
 
 

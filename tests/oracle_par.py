@@ -55,6 +55,19 @@ def knn(Vq: np.ndarray, Vs: np.ndarray, k: int):
     return ids, dist
 
 
+def knn_i8q(Q8: np.ndarray, Vs: np.ndarray, k: int):
+    nq = Q8.shape[0]
+    ids = np.empty((nq, k), dtype=np.int64)
+    score = np.empty((nq, k), dtype=np.int32)
+
+    def job(q):
+        ids[q:q + 1], score[q:q + 1] = oracle.knn_i8q(Q8[q:q + 1], Vs, k)
+
+    with cf.ThreadPoolExecutor(min(THREADS, nq)) as ex:
+        list(ex.map(job, range(nq)))
+    return ids, score
+
+
 def check_knn_sampled(Vq_row, ids_row, dist_row, V_returned, V_sample, sample_idx):
     """Properties that hold at any size, checked by the oracle one row at a time:
     the returned distances are the oracle's Delta of the returned rows, the
