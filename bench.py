@@ -57,6 +57,9 @@ def parse():
                     help="instead of the benchmark: recall of the ternary scan against exact "
                          "float32 cosine kNN for several x (1M x 768 mixture by default)")
     ap.add_argument("--sweep-queries", type=int, default=2000)
+    ap.add_argument("--spearman", action="store_true",
+                    help="instead of the benchmark: Table 1's Uniform rows (Spearman rho of "
+                         "EVP, 1-bit and b1.58 proxy distances) through the library")
     return ap.parse_args()
 
 
@@ -526,8 +529,83 @@ def main_recall_sweep(a):
     print(json.dumps(out))
 
 
+def pack_ternary_torch(V):
+    """Comparator helper: ternary int tensor [n, d] -> packed codes [n, 2W]
+    (v+ words then v- words, bit j of word j // 64).  Used only for the
+    b1.58 comparator codes, which the library does not produce."""
+    import torch
+    n, d = V.shape
+    W = (d + 63) // 64
+    pad = torch.zeros((n, 64 * W), dtype=torch.int64, device=V.device)
+    pad[:, :d] = V.to(torch.int64)
+    weights = torch.ones(64, dtype=torch.int64, device=V.device)
+    weights[1:] = 2 ** torch.arange(1, 64, device=V.device, dtype=torch.int64)
+    weights[63] = -(2 ** 63)
+    p = ((pad == 1).to(torch.int64).view(n, W, 64) * weights).sum(-1)
+    m = ((pad == -1).to(torch.int64).view(n, W, 64) * weights).sum(-1)
+    return torch.cat([p, m], 1).contiguous()
+
+
+def spearman_study(evp, synth, dev, d, nq=100, ns=1000):
+    """Table 1's 'Uniform' rows through the library: uniform points on the
+    sphere; proxy distances of all nq x ns pairs from the GPU scan (popcount
+    path, exact ||q - s||^2 for any ternary codes) for the {x,d} EVP codes
+    (evp_encode at the default x), the 1-bit codes ({d,d} EVP, evp_encode
+    at x = d) and the b1.58 codes (comparator, per-vector absmean gamma);
+    Spearman rho of each against the true Euclidean distance."""
+    import torch
+    from scipy.stats import spearmanr
+    U = synth.uniform_sphere(nq + ns, d, stream=30 + d)
+    Ud = torch.from_numpy(U).to(dev)
+    true = np.linalg.norm(U[:nq, None, :].astype(np.float64) - U[None, nq:, :], axis=2)
+
+    def all_pairs(T, x):
+        ids, dist = evp.ternary_knn(T[:nq].contiguous(), T[nq:].contiguous(), d, x, ns,
+                                    path=evp.PATH_POPC)
+        D = torch.empty((nq, ns), dtype=torch.int32, device=dev)
+        D.scatter_(1, ids, dist)
+        return D.cpu().numpy()
+
+    x = evp.default_x(d)
+    st = evp.new_status(dev)
+    D_evp = all_pairs(evp.encode(Ud, x, status=st), x)
+    D_one = all_pairs(evp.encode(Ud, d, status=st), d)
+    gamma = Ud.abs().mean(1, keepdim=True)
+    B = torch.clamp(torch.round(Ud / (gamma + 1e-8)), -1, 1)
+    D_b158 = all_pairs(pack_ternary_torch(B), d)
+    torch.cuda.synchronize()
+    evp.check_status(st, "spearman encode")
+    t = true.ravel()
+    return {"d": d, "x": x, "pairs": nq * ns,
+            "rho_evp": float(spearmanr(t, D_evp.ravel()).correlation),
+            "rho_1bit": float(spearmanr(t, D_one.ravel()).correlation),
+            "rho_b158": float(spearmanr(t, D_b158.ravel()).correlation),
+            "D_evp": D_evp, "true": true}
+
+
+def main_spearman(a):
+    """Table 1 ('Uniform-100', 'Uniform-1000') reproduced through the library."""
+    import torch
+    from paper_2506_00528_gb300 import build as _build
+    from paper_2506_00528_gb300 import evp, synth
+    _build.build()
+    evp.load()
+    dev = torch.device("cuda", 0)
+    paper = {100: (0.80, 0.70, 0.75), 1000: (0.79, 0.64, 0.71)}
+    rows = []
+    for d in (100, 1000):
+        r = spearman_study(evp, synth, dev, d)
+        rows.append({k: v for k, v in r.items() if k not in ("D_evp", "true")} |
+                    {"paper_evp_1bit_b158": paper[d]})
+    print(json.dumps({"kind": "spearman", "data": "uniform points on the unit sphere "
+                      "(the paper's Uniform rows), 100 x 1000 pairs per d",
+                      "rows": rows}))
+
+
 def main():
     a = parse()
+    if a.spearman:
+        return main_spearman(a)
     if a.impl == "reference":
         return main_reference(a)
     if a.recall_sweep:

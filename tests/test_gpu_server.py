@@ -1,5 +1,6 @@
 """Continuous-batching server: every request's result is bit-identical to
-the same request run alone through evp_db_search_host; admission by memory;
+the same request run alone through evp_db_search_host, and agrees with the
+oracle (exhaustive shortlist by Delta, float64 rerank); admission by memory;
 a stalled worker (paused on the host) makes waits time out."""
 import threading
 
@@ -7,7 +8,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2506_00528_gb300 import synth
+from test_gpu_rerank import check_rerank
 
 pytestmark = pytest.mark.gpu
 
@@ -19,6 +22,7 @@ def served_db(dev, evp_lib):
     Ud = torch.from_numpy(U).to(dev)
     T = evp_lib.encode(Ud, x)
     db = evp_lib.Database(T, Ud, d, x)
+    db.U_host, db.V_oracle = U, oracle.encode(U, x)
     yield db
     db.close()
 
@@ -63,11 +67,15 @@ def test_mixed_requests_match_alone(evp_lib, served_db):
     srv.close()
     assert stats["requests"] == len(reqs) and stats["p99_us"] >= stats["p50_us"] > 0
     assert stats["batches"] < len(reqs)            # requests were coalesced
-    for (Q, k), (ids, sc, status, lat) in zip(reqs, out):
+    for i, ((Q, k), (ids, sc, status, lat)) in enumerate(zip(reqs, out)):
         assert status == 0 and lat > 0
         ai, asc = _alone(evp_lib, served_db, Q, k, 10)
         assert torch.equal(ids, ai)
         assert torch.equal(sc, asc)
+        if i % 4 == 0:
+            # the oracle: exhaustive shortlist of 10 k by Delta, float64 rerank to k
+            sl, _ = oracle.knn(oracle.encode(Q, served_db.x), served_db.V_oracle, 10 * k)
+            check_rerank(ids.numpy(), sc.numpy(), Q, served_db.U_host, sl, k)
 
 
 def test_admission_by_memory(evp_lib, served_db):
