@@ -407,21 +407,38 @@ int32_t evp_db_search_host(evp_db_t db, const float* Q_host, int64_t nq, int32_t
  *
  * evp_autotune times the popcount and both tensor-core scans (where they
  * apply) on a database for a query count (rounded up to a power of two)
- * and k, using the database's own rows as trial queries, and caches the
- * fastest path per (database, query-count bucket, k); *path_out receives
- * it, *popc_ms (optional) the popcount time and *mma_ms (optional) the
- * faster tensor-core time; asking for a timing forces a fresh measurement.
- * It allocates temporary device memory.
+ * and k, using the database's own rows as trial queries, and keeps the
+ * fastest path per (GPU model, d, x, query-count bucket, k, row-count
+ * bucket); *path_out receives it, *popc_ms (optional) the popcount time
+ * and *mma_ms (optional) the faster tensor-core time; asking for a timing
+ * forces a fresh measurement.  It allocates temporary device memory.
+ * evp_autotune_save / evp_autotune_load write and read the tuner's
+ * decisions (paths and fused tile shapes) as a text file, one "key value"
+ * line each, so that a deployment tunes once per GPU model; loading merges
+ * into the current table.  evp_autotune_clear empties it.
  *
  * evp_batch_plan_create checks every descriptor, picks each batch's path
- * with evp_autotune (EVP_BATCH_NO_TUNE: the automatic rule instead), and
- * allocates one workspace region per batch (the plan owns it).
- * evp_batch_run enqueues all batches on `stream`, dealing them over four
- * forked streams that join back into `stream`; with EVP_BATCH_GRAPH the
- * first run captures this into a CUDA graph (`stream` must not be the
- * legacy default stream) and every run launches the graph.  Results equal
- * the per-batch evp_db_search / evp_db_knn calls.  dev_status is shared by
- * all batches (and baked into the graph at capture).
+ * with evp_autotune (EVP_BATCH_NO_TUNE: the automatic rule instead) and
+ * allocates one workspace region per batch (the plan owns it).  Every batch
+ * whose path is the e4m3 tensor-core scan (EVP_PATH_MMA) and whose database
+ * holds its tensor copy (EVP_DB_TENSOR_COPY) joins the fused scan (at most
+ * 64 batches): one persistent launch over the work items -- (batch, query
+ * unit, database slice) -- of all of them, after one launch that prepares
+ * all their queries and before one final merge of all their queries.  The
+ * fused scan's tile shape (database tiles per work item, scaled by each
+ * batch's d so that items cost about the same) is timed on the plan's own
+ * batches among a few candidates and remembered by the tuner
+ * (EVP_BATCH_NO_TUNE: a fixed shape).  EVP_BATCH_SEPARATE runs every batch
+ * with its own calls instead.
+ * evp_batch_run enqueues all batches on `stream`: the fused scan there, the
+ * other batches dealt over four forked streams that join back into
+ * `stream`; with EVP_BATCH_GRAPH the first run captures this into a CUDA
+ * graph (`stream` must not be the legacy default stream) and every run
+ * launches the graph.  Results equal the per-batch evp_db_search /
+ * evp_db_knn calls.  dev_status is shared by all batches (and baked into the
+ * graph at capture).  evp_batch_plan_fused returns how many batches the
+ * fused scan takes, evp_batch_plan_tile the tile shape of batch i (0 when
+ * it is not fused).
  * ------------------------------------------------------------------- */
 typedef struct {
     evp_db_t db;
@@ -435,15 +452,20 @@ typedef struct {
     int32_t* dist;        /* plain kNN: [nq][k] Delta                         */
 } evp_batch_desc;
 typedef struct evp_batch_plan* evp_batch_plan_t;
-#define EVP_BATCH_GRAPH   1
-#define EVP_BATCH_NO_TUNE 2
+#define EVP_BATCH_GRAPH    1
+#define EVP_BATCH_NO_TUNE  2
+#define EVP_BATCH_SEPARATE 4
 
 int32_t evp_autotune(evp_db_t db, int64_t nq, int32_t k, int32_t* path_out, float* popc_ms,
                      float* mma_ms, void* stream);
 int32_t evp_autotune_clear(void);
+int32_t evp_autotune_save(const char* path);
+int32_t evp_autotune_load(const char* path);
 int32_t evp_batch_plan_create(const evp_batch_desc* batches, int32_t nb, int32_t flags,
                               void* stream, evp_batch_plan_t* out);
 int32_t evp_batch_plan_path(evp_batch_plan_t plan, int32_t i);   /* chosen path of batch i */
+int32_t evp_batch_plan_fused(evp_batch_plan_t plan);
+int32_t evp_batch_plan_tile(evp_batch_plan_t plan, int32_t i);
 size_t evp_batch_plan_workspace(evp_batch_plan_t plan);
 int32_t evp_batch_run(evp_batch_plan_t plan, int32_t* dev_status, void* stream);
 int32_t evp_batch_plan_destroy(evp_batch_plan_t plan);

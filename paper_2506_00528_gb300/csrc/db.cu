@@ -45,6 +45,12 @@ SearchLayout search_layout(const evp_db* db, int64_t nq, int32_t n_shortlist,
 
 }  // namespace
 
+namespace evp {
+const uint8_t* db_tensor_copy(const evp_db* db) { return db ? db->S8 : nullptr; }
+const float* db_float_rows(const evp_db* db) { return db ? db->U : nullptr; }
+int db_x(const evp_db* db) { return db ? db->x : 0; }
+}  // namespace evp
+
 extern "C" {
 
 int32_t evp_db_create(const uint64_t* T, const float* U, int64_t ns, int32_t d, int32_t x,

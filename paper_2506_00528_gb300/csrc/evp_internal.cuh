@@ -277,6 +277,26 @@ int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uin
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
                            cudaStream_t stream, int bin_shift = -1, int dist_bias = 0);
 
+// One batch of a multi-batch final merge: queries q0 .. q0 + nq - 1 of the
+// launch are queries 0 .. nq - 1 of this batch (Delta keys).
+struct FmBatch {
+    const uint64_t* lists;
+    const int32_t* meta;
+    const uint64_t* tau;
+    const uint32_t* hist;
+    const uint32_t* minhalf;
+    int hist_bins, nslices, k, stage;
+    int64_t q0;
+    int64_t* ids;
+    int32_t* dist;
+};
+// Shared-memory bytes of a final merge of nslices lists of k keys, and
+// whether it stages the lists (*stage).
+size_t final_merge_smem(int nslices, int k, int* stage);
+// tab: device array of nb + 1 entries (the last only supplies q0 = total).
+int32_t launch_final_merge_multi(const FmBatch* tab, int nb, int64_t total_q, size_t smem,
+                                 cudaStream_t stream);
+
 // int8 queries (the single-operand translation of Sec. 6).
 cudaError_t launch_quantize_i8(const float* Q, int64_t n, int d, int8_t* Q8, int32_t* status,
                                cudaStream_t stream);
@@ -315,7 +335,33 @@ int mma_kp(int d);
 // the same other arguments) on `path` (AUTO resolved per call).
 size_t knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert_db);
 int mma_active_queries(int k);
-MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db);
+// tiles_per_item > 0: slices of about that many 256-row database tiles (the
+// tile shape of the fused multi-batch scan) instead of whole waves.
+MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
+                      int tiles_per_item = 0);
+
+// Fused multi-batch tensor-core scan (the batched form): several kNN
+// batches, each against a resident e4m3 database copy, scanned by one
+// persistent launch over the work items of all of them, then merged by one
+// multi-batch final merge.  The plan owns a small device table (tensor maps,
+// per-batch arguments) written once at creation; workspaces are the
+// caller's.
+struct MmaBatchSpec {
+    const uint64_t* Q;   // packed query codes [nq][2W]
+    int64_t nq;
+    const uint8_t* S8;   // resident e4m3 copy of the database [ns][kp], 256-byte aligned
+    int64_t ns;
+    int d, x, k;
+    int64_t* ids;        // [nq][k]
+    int32_t* dist;       // [nq][k]
+    void* ws;            // mma_multi_ws(...) bytes, 256-byte aligned
+    int tiles_per_item;  // tile shape: 256-row database tiles per work item
+};
+struct MmaMultiPlan;
+size_t mma_multi_ws(int64_t nq, int64_t ns, int d, int k, int tiles_per_item);
+int32_t mma_multi_create(const MmaBatchSpec* specs, int nb, MmaMultiPlan** out);
+int32_t mma_multi_run(MmaMultiPlan* p, int32_t* status, cudaStream_t stream);
+void mma_multi_destroy(MmaMultiPlan* p);
 // spread_cg > 0: query rows placed as the tensor-core scan's small-batch
 // spread over spread_cg CTAs expects (queries only).
 cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
@@ -350,6 +396,12 @@ cudaError_t launch_pack_sparse(const uint64_t* T, int64_t n, int d, int x, uint1
 int32_t run_sparse_knn(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t ns, int d,
                        int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                        int32_t* status, cudaStream_t stream);
+
+// Internals of a resident database (db.cu): its e4m3 copy (null without
+// EVP_DB_TENSOR_COPY), its float rows (may be null) and its x.
+const uint8_t* db_tensor_copy(const evp_db* db);
+const float* db_float_rows(const evp_db* db);
+int db_x(const evp_db* db);
 
 // Path the automatic rule takes for nq queries (resident_copy: the
 // database's e4m3 copy is resident).

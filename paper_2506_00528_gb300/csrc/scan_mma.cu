@@ -48,6 +48,9 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
 
 namespace evp {
 
@@ -114,6 +117,21 @@ struct MmaArgs {
     int hist_bins;         // 2x + 1
     int32_t* status;
     int stall_fills;       // testing: CTA 0's producer stops after this many fills (-1: never)
+};
+
+// Multi-batch form (the batched plan's fused scan): one persistent launch
+// whose work items are the (query unit, database slice) items of several
+// batches, each batch against its own resident database.  Items are
+// numbered batch after batch; batch b owns items [item0[b], item0[b+1]).
+// Each item reads its batch's arguments and tensor maps from this table in
+// device memory (written once by the host before the first launch).
+constexpr int MMA_MULTI_MAX = 64;
+struct MmaMulti {  // 64-byte aligned through its tensor maps
+    CUtensorMap mapA[MMA_MULTI_MAX];  // query operand of each batch
+    CUtensorMap mapB[MMA_MULTI_MAX];  // database operand of each batch
+    MmaArgs args[MMA_MULTI_MAX];
+    int item0[MMA_MULTI_MAX + 1];
+    int nbatches, nitems;
 };
 
 // Maximum of three floats in one instruction (no NaN among the inputs here).
@@ -275,10 +293,12 @@ __device__ __forceinline__ void heap_push(uint32_t* h, int qa, int m, int n, uin
     h[i * qa + m] = key;
 }
 
-template <int CG>
+// MULTI = false: one batch, arguments a and maps tmA/tmB.  MULTI = true:
+// the items of every batch of `multi`; a supplies only the status word.
+template <int CG, bool MULTI>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                const MmaArgs a) {
+                const __grid_constant__ MmaArgs a, const MmaMulti* __restrict__ multi) {
     using C = MmaCfg<CG>;
     constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
@@ -305,27 +325,45 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int* peer_fills = abort_flag + 4; // CG = 2: the same count of the other CTA
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nslices = a.nslices;
     // CTA pair: rank 0 issues the MMAs; both run every other role.
     const uint32_t rank = CG == 2 ? cluster_ctarank() : 0u;
     const bool leader = rank == 0;
     const int worker = (int)blockIdx.x / CG, nworkers = (int)gridDim.x / CG;
-    const int units = (a.qtiles + CG - 1) / CG;  // query tiles (CG = 1) or tile pairs per slice
-    const int nitems = units * a.nslices;
-    const int kchunks = a.kchunks;
-    // Work item -> (query unit, database slice); this CTA takes query tile
-    // unit * CG + rank.  Consecutive items share a slice, so the CTAs of one
-    // wave that work on the same slice read its rows from L2 rather than HBM.
+    const int nitems = MULTI ? multi->nitems : ((a.qtiles + CG - 1) / CG) * a.nslices;
+    // Work item -> (batch, query unit, database slice); this CTA takes query
+    // tile unit * CG + rank.  Consecutive items share a slice, so the CTAs of
+    // one wave that work on the same slice read its rows from L2 rather than
+    // HBM.
     struct Item {
-        int qt, slice, ntiles;
+        int b, qt, slice, ntiles;
         int64_t row0, row_end;
+    };
+    // (the address of a __grid_constant__ parameter is valid for the whole kernel)
+    const MmaArgs* const a_param = &a;
+    auto args_of = [&](int b) -> const MmaArgs& {
+        if constexpr (MULTI) return multi->args[b];
+        else return *a_param;
     };
     auto item_of = [&](int item) {
         Item w;
-        w.qt = (item % units) * CG + (int)rank;
-        w.slice = item / units;
-        w.row0 = (int64_t)w.slice * a.rows_per_slice;
-        w.row_end = min(w.row0 + a.rows_per_slice, a.ns);
+        w.b = 0;
+        int li = item;
+        if constexpr (MULTI) {
+            int lo = 0, hi = multi->nbatches - 1;  // last batch with item0 <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (multi->item0[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            w.b = lo;
+            li = item - multi->item0[lo];
+        }
+        const MmaArgs& A = args_of(w.b);
+        const int units = (A.qtiles + CG - 1) / CG;  // query tiles (CG = 1) or tile pairs per slice
+        w.qt = (li % units) * CG + (int)rank;
+        w.slice = li / units;
+        w.row0 = (int64_t)w.slice * A.rows_per_slice;
+        w.row_end = min(w.row0 + A.rows_per_slice, A.ns);
         w.ntiles = w.row_end > w.row0 ? (int)((w.row_end - w.row0 + MMA_N - 1) / MMA_N) : 0;
         return w;
     };
@@ -384,6 +422,14 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             bool ok = true;
             for (int item = worker; item < nitems && ok; item += nworkers) {
                 const Item w = item_of(item);
+                const MmaArgs& a = args_of(w.b);
+                const int kchunks = a.kchunks;
+                const CUtensorMap* mapA = &tmA;
+                const CUtensorMap* mapB = &tmB;
+                if constexpr (MULTI) {
+                    mapA = &multi->mapA[w.b];
+                    mapB = &multi->mapB[w.b];
+                }
                 // a tile past the last query (odd tile count) loads tile 0; its rows are ignored
                 const int32_t arow = w.qt < a.qtiles ? w.qt * a.qa : 0;
                 for (int t = 0; t < w.ntiles && ok; ++t) {
@@ -408,13 +454,13 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         uint8_t* st = stages + s * STAGE_BYTES;
                         if constexpr (CG == 1) {
                             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                            tma_load_2d(st, &tmA, &full[s], kc * KCHUNK, arow);
-                            tma_load_2d(st + A_STAGE_BYTES, &tmB, &full[s], kc * KCHUNK, brow);
+                            tma_load_2d(st, mapA, &full[s], kc * KCHUNK, arow);
+                            tma_load_2d(st + A_STAGE_BYTES, mapB, &full[s], kc * KCHUNK, brow);
                         } else {
                             if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
                             const uint32_t fb = peer_addr(&full[s], 0u);
-                            tma_load_2d_pair(st, &tmA, fb, kc * KCHUNK, arow);
-                            tma_load_2d_pair(st + A_STAGE_BYTES, &tmB, fb, kc * KCHUNK, brow);
+                            tma_load_2d_pair(st, mapA, fb, kc * KCHUNK, arow);
+                            tma_load_2d_pair(st + A_STAGE_BYTES, mapB, fb, kc * KCHUNK, brow);
                         }
                     }
                 }
@@ -441,6 +487,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             bool ok = true;
             for (int item = worker; item < nitems && ok; item += nworkers) {
               const Item w = item_of(item);
+              const int kchunks = args_of(w.b).kchunks;
               for (int t = 0; t < w.ntiles && ok; ++t, ++tt) {
                 const int b = tt & 1;
                 const uint32_t use = (uint32_t)(tt >> 1);
@@ -482,7 +529,6 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
         const int m = quarter * 32 + lane;  // TMEM lane = query row in the tile
-        const int k = a.k;
         int tt = 0;  // accumulator tiles consumed so far (all items)
         bool ok = true;
         // accumulator release: the leader's barrier (in the other CTA for rank 1)
@@ -490,6 +536,8 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const uint32_t acc_empty1 = CG == 2 ? peer_addr(&acc_empty[1], 0u) : 0u;
         for (int item = worker; item < nitems && ok; item += nworkers) {
         const Item w = item_of(item);
+        const MmaArgs& a = args_of(w.b);
+        const int k = a.k, nslices = a.nslices;
         const int slice = w.slice, ntiles = w.ntiles;
         const int64_t row0 = w.row0, row_end = w.row_end;
         const int qa = a.qa;
@@ -597,7 +645,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                             // D is an integer below 2^22 in magnitude: adding
                             // 1.5 * 2^23 leaves it in the low mantissa bits
                             const int di = __float_as_int(dv + 12582912.0f) - 0x4B400000;
-                            const uint32_t half_delta = (uint32_t)(a.x - di);
+                            // clamped: a code without exactly x non-zeros must not
+                            // index outside the histogram
+                            const uint32_t half_delta = (uint32_t)min(max(a.x - di, 0), 2 * a.x);
                             staging[sc * MMA_M + m] = (half_delta << LOCAL_BITS) | (gbase + (uint32_t)j);
                             ++sc;
                         }
@@ -686,7 +736,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 for (int j = 0; j < MMA_M / 32; ++j) best[j] = 0xFFFFFFFFu;
                 seen = item;
             }
-            const int qt = item_of(item).qt;
+            const Item wi = item_of(item);
+            const MmaArgs& a = args_of(wi.b);
+            const int qt = wi.qt;
 #pragma unroll 1
             for (int j = 0; j < MMA_M / 32; ++j) {
                 const int mm = j * 32 + lane;
@@ -837,7 +889,7 @@ int mma_pair_workers() {
     }
     if (!known[dev]) {
         int n = 0;
-        if (cudaFuncSetAttribute(scan_mma_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(scan_mma_kernel<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)MmaCfg<2>::SMEM_BYTES) == cudaSuccess) {
             cudaLaunchConfig_t cfg = {};
             cudaLaunchAttribute attr[1];
@@ -850,7 +902,7 @@ int mma_pair_workers() {
             cfg.dynamicSmemBytes = MmaCfg<2>::SMEM_BYTES;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            if (cudaOccupancyMaxActiveClusters(&n, scan_mma_kernel<2>, &cfg) != cudaSuccess) n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, scan_mma_kernel<2, false>, &cfg) != cudaSuccess) n = 0;
         }
         cudaGetLastError();
         cached[dev] = std::max(0, n);
@@ -859,7 +911,8 @@ int mma_pair_workers() {
     return cached[dev];
 }
 
-MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
+MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
+                      int tiles_per_item) {
     MmaPlan p{};
     p.kp = mma_kp(d);
     p.qa = mma_active_queries(k);
@@ -886,6 +939,9 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db) {
     const int64_t step = sms / g;
     int64_t slices = step;
     while (slices < min_slices) slices += step;
+    // a given tile shape (the fused multi-batch scan): slices of about
+    // tiles_per_item database tiles each
+    if (tiles_per_item > 0) slices = std::max(min_slices, (ntiles + tiles_per_item - 1) / tiles_per_item);
     slices = std::min(slices, std::max<int64_t>(1, ntiles));
     const int64_t tiles_per_slice = (ntiles + slices - 1) / slices;
     p.rows_per_slice = tiles_per_slice * MMA_N;
@@ -981,12 +1037,12 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.stall_fills = take_stall_mma();
     const int items = (p.qtiles + p.cg - 1) / p.cg * p.nslices;
     if (p.cg == 1) {
-        if (cudaFuncSetAttribute(scan_mma_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(scan_mma_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)MmaCfg<1>::SMEM_BYTES) != cudaSuccess)
             return EVP_ERR_CUDA;
         TimedLaunch timer("scan_mma", stream);
-        scan_mma_kernel<1><<<std::min(items, p.workers), NUM_THREADS, MmaCfg<1>::SMEM_BYTES,
-                             stream>>>(tmA, tmB, args);
+        scan_mma_kernel<1, false><<<std::min(items, p.workers), NUM_THREADS, MmaCfg<1>::SMEM_BYTES,
+                                    stream>>>(tmA, tmB, args, nullptr);
     } else {
         // attribute already set by mma_pair_workers
         cudaLaunchConfig_t cfg = {};
@@ -1002,12 +1058,272 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
         cfg.attrs = attr;
         cfg.numAttrs = 1;
         TimedLaunch timer("scan_mma", stream);
-        if (cudaLaunchKernelEx(&cfg, scan_mma_kernel<2>, tmA, tmB, args) != cudaSuccess)
+        if (cudaLaunchKernelEx(&cfg, scan_mma_kernel<2, false>, tmA, tmB, args,
+                               static_cast<const MmaMulti*>(nullptr)) != cudaSuccess)
             return EVP_ERR_CUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
     return launch_final_merge(lists, meta, tau, hist, minhalf, hist_bins, nq, p.nslices, k, ids,
                               dist, stream);
+}
+
+
+// ---- fused multi-batch scan -------------------------------------------------
+namespace {
+
+struct PrepBatch {
+    const uint64_t* Q;    // packed query codes [nq][2W]
+    int64_t nq, rows;     // queries, and rows of the e4m3 query operand written
+    int W, Kp, spread_cg;
+    uint8_t* A8;          // [rows][Kp] e4m3 query operand
+    uint64_t* tau;        // [nq]
+    uint32_t* minhalf;    // [nq]
+    uint32_t* hist;       // [hist_words]
+    int64_t hist_words;
+};
+
+// One launch prepares every batch (blockIdx.y = batch): each row of the
+// query operand is written once -- the unpacked query whose lane it is, or
+// zeros for an unused lane of a spread batch -- and the thresholds, minima
+// and histograms of the union bound start empty.
+__global__ void multi_prep_kernel(const PrepBatch* __restrict__ tab) {
+    const PrepBatch& p = tab[blockIdx.y];
+    const int groups = p.Kp / 16;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t idx = i0; idx < p.rows * groups; idx += stride) {
+        const int64_t R = idx / groups;
+        const int g = (int)(idx - R * groups);
+        const int64_t q = p.spread_cg > 0 ? query_of_lane((int)(R & 127), (int)(R >> 7), p.spread_cg) : R;
+        uint32_t o[4] = {0u, 0u, 0u, 0u};
+        const int j0 = g * 16, w = j0 >> 6, sh = j0 & 63;
+        if (q < p.nq && w < p.W) {
+            const uint32_t pp = (uint32_t)((p.Q[q * 2 * p.W + w] >> sh) & 0xFFFFu);
+            const uint32_t mm = (uint32_t)((p.Q[q * 2 * p.W + p.W + w] >> sh) & 0xFFFFu);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int e = i * 4 + b;
+                    const uint32_t byte = ((pp >> e) & 1u) ? 0x38u : (((mm >> e) & 1u) ? 0xB8u : 0u);
+                    o[i] |= byte << (8 * b);
+                }
+            }
+        }
+        reinterpret_cast<uint4*>(p.A8 + R * (int64_t)p.Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+    for (int64_t i = i0; i < p.nq; i += stride) {
+        p.tau[i] = KEY_NONE;
+        p.minhalf[i] = 0xFFFFFFFFu;
+    }
+    for (int64_t i = i0; i < p.hist_words; i += stride) p.hist[i] = 0u;
+}
+
+struct MultiLayout {
+    MmaPlan p;
+    uint8_t* A8;
+    uint64_t* lists;
+    int32_t* meta;
+    uint64_t* tau;
+    uint32_t* hist;
+    uint32_t* minhalf;
+};
+
+MultiLayout multi_layout(const MmaBatchSpec& b, int tiles_per_item) {
+    MultiLayout L;
+    L.p = plan_mma_scan(b.nq, b.ns, b.d, b.k, false, tiles_per_item);
+    uint8_t* w = static_cast<uint8_t*>(b.ws);
+    L.A8 = w;
+    L.lists = reinterpret_cast<uint64_t*>(w + L.p.a_bytes);
+    L.meta = reinterpret_cast<int32_t*>(w + L.p.a_bytes + L.p.list_bytes);
+    L.tau = reinterpret_cast<uint64_t*>(w + L.p.a_bytes + L.p.list_bytes + L.p.meta_bytes);
+    L.hist = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(L.tau) + L.p.tau_bytes);
+    L.minhalf = reinterpret_cast<uint32_t*>(reinterpret_cast<uint8_t*>(L.hist) +
+                                            align256((size_t)b.nq * (2 * b.d + 1) * 4));
+    return L;
+}
+
+}  // namespace
+
+struct MmaMultiPlan {
+    int nb = 0, cg = 1, workers = 0;
+    int64_t total_q = 0;
+    size_t fm_smem = 0;
+    MmaMulti* table = nullptr;   // device
+    PrepBatch* prep = nullptr;   // device [nb]
+    FmBatch* fm = nullptr;       // device [nb + 1]
+    int max_rows_groups = 0;
+    int32_t* status_slot = nullptr;
+};
+
+size_t mma_multi_ws(int64_t nq, int64_t ns, int d, int k, int tiles_per_item) {
+    return plan_mma_scan(nq, ns, d, k, false, tiles_per_item).ws_bytes;
+}
+
+int32_t mma_multi_create(const MmaBatchSpec* specs, int nb, MmaMultiPlan** out) {
+    *out = nullptr;
+    if (nb < 1 || nb > MMA_MULTI_MAX) return EVP_ERR_UNSUPPORTED;
+    EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return EVP_ERR_CUDA;
+    MmaMulti* h = new (std::nothrow) MmaMulti();
+    if (!h) return EVP_ERR_NO_MEMORY;
+    std::vector<PrepBatch> prep(nb);
+    std::vector<FmBatch> fm(nb + 1);
+    MmaMultiPlan* P = new (std::nothrow) MmaMultiPlan();
+    if (!P) {
+        delete h;
+        return EVP_ERR_NO_MEMORY;
+    }
+    int items = 0;
+    size_t fm_smem = 0;
+    int64_t q0 = 0;
+    int32_t rc = EVP_OK;
+    for (int b = 0; b < nb && rc == EVP_OK; ++b) {
+        const MmaBatchSpec& B = specs[b];
+        if (!B.Q || B.nq < 1 || !B.S8 || B.k < 1 || B.k > MMA_K_MAX || !B.ids || !B.dist || !B.ws ||
+            (reinterpret_cast<uintptr_t>(B.S8) & 255) != 0) {
+            rc = EVP_ERR_INVALID;
+            break;
+        }
+        const MultiLayout L = multi_layout(B, B.tiles_per_item);
+        const MmaPlan& p = L.p;
+        if (b == 0) {
+            P->cg = p.cg;
+            P->workers = p.workers;
+        }
+        const int64_t arows = p.spread ? (int64_t)p.qtiles * MMA_M : B.nq;
+        CUtensorMap* tmA = &h->mapA[b];
+        CUtensorMap* tmB = &h->mapB[b];
+        cuuint64_t gdimA[2] = {(cuuint64_t)p.kp, (cuuint64_t)arows};
+        cuuint64_t gdimB[2] = {(cuuint64_t)p.kp, (cuuint64_t)B.ns};
+        cuuint64_t gstride[1] = {(cuuint64_t)p.kp};
+        cuuint32_t boxA[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)MMA_M};
+        cuuint32_t boxB[2] = {(cuuint32_t)KCHUNK, (cuuint32_t)(MMA_N / p.cg)};
+        cuuint32_t es[2] = {1, 1};
+        if (enc(tmA, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, L.A8, gdimA, gstride, boxA, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+            enc(tmB, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<uint8_t*>(B.S8), gdimB, gstride,
+                boxB, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+            rc = EVP_ERR_CUDA;
+            break;
+        }
+        MmaArgs& A = h->args[b];
+        A = MmaArgs{};
+        A.nq = (int)B.nq;
+        A.ns = B.ns;
+        A.kchunks = p.kp / KCHUNK;
+        A.x = B.x;
+        A.k = B.k;
+        A.rows_per_slice = p.rows_per_slice;
+        A.qtiles = p.qtiles;
+        A.qa = p.qa;
+        A.spread = p.spread ? 1 : 0;
+        A.nslices = p.nslices;
+        A.lists = L.lists;
+        A.meta = L.meta;
+        A.tau_global = L.tau;
+        A.hist = L.hist;
+        A.minhalf = L.minhalf;
+        A.hist_bins = 2 * B.x + 1;
+        A.status = nullptr;
+        A.stall_fills = -1;
+        h->item0[b] = items;
+        items += (p.qtiles + p.cg - 1) / p.cg * p.nslices;
+        prep[b] = PrepBatch{B.Q, B.nq, arows, (B.d + 63) / 64, p.kp, p.spread ? p.cg : 0, L.A8,
+                            L.tau, L.minhalf, L.hist, B.nq * (int64_t)A.hist_bins};
+        int stage = 0;
+        fm_smem = std::max(fm_smem, final_merge_smem(p.nslices, B.k, &stage));
+        fm[b] = FmBatch{L.lists, L.meta, L.tau, L.hist, L.minhalf, A.hist_bins, p.nslices, B.k,
+                        stage, q0, B.ids, B.dist};
+        q0 += B.nq;
+        P->max_rows_groups = std::max<int>(P->max_rows_groups, (int)std::min<int64_t>(
+                                               arows * (p.kp / 16), 1 << 30));
+    }
+    if (rc == EVP_OK) {
+        h->item0[nb] = items;
+        h->nbatches = nb;
+        h->nitems = items;
+        fm[nb] = FmBatch{};
+        fm[nb].q0 = q0;
+        P->nb = nb;
+        P->total_q = q0;
+        P->fm_smem = fm_smem;
+        if (cudaMalloc(&P->table, sizeof(MmaMulti)) != cudaSuccess ||
+            cudaMalloc(&P->prep, sizeof(PrepBatch) * nb) != cudaSuccess ||
+            cudaMalloc(&P->fm, sizeof(FmBatch) * (nb + 1)) != cudaSuccess) {
+            cudaGetLastError();
+            rc = EVP_ERR_NO_MEMORY;
+        } else if (cudaMemcpy(P->table, h, sizeof(MmaMulti), cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(P->prep, prep.data(), sizeof(PrepBatch) * nb,
+                              cudaMemcpyHostToDevice) != cudaSuccess ||
+                   cudaMemcpy(P->fm, fm.data(), sizeof(FmBatch) * (nb + 1),
+                              cudaMemcpyHostToDevice) != cudaSuccess) {
+            rc = EVP_ERR_CUDA;
+        }
+    }
+    delete h;
+    if (rc != EVP_OK) {
+        mma_multi_destroy(P);
+        return rc;
+    }
+    *out = P;
+    return EVP_OK;
+}
+
+int32_t mma_multi_run(MmaMultiPlan* P, int32_t* status, cudaStream_t stream) {
+    if (!P) return EVP_ERR_INVALID;
+    {
+        TimedLaunch timer("unpack_fp8", stream);
+        const int64_t bx = std::min<int64_t>((P->max_rows_groups + 255) / 256, (int64_t)num_sms() * 4);
+        multi_prep_kernel<<<dim3((unsigned)std::max<int64_t>(1, bx), (unsigned)P->nb), 256, 0,
+                            stream>>>(P->prep);
+        if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
+    }
+    MmaArgs a{};      // the launch's status word (the table's arguments hold the rest)
+    a.status = status;
+    a.stall_fills = -1;
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    if (P->cg == 1) {
+        if (cudaFuncSetAttribute(scan_mma_kernel<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MmaCfg<1>::SMEM_BYTES) != cudaSuccess)
+            return EVP_ERR_CUDA;
+        TimedLaunch timer("scan_mma", stream);
+        scan_mma_kernel<1, true><<<P->workers, NUM_THREADS, MmaCfg<1>::SMEM_BYTES, stream>>>(
+            dummy, dummy, a, P->table);
+    } else {
+        if (cudaFuncSetAttribute(scan_mma_kernel<2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)MmaCfg<2>::SMEM_BYTES) != cudaSuccess)
+            return EVP_ERR_CUDA;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2 * (unsigned)P->workers);
+        cfg.blockDim = dim3(NUM_THREADS);
+        cfg.dynamicSmemBytes = MmaCfg<2>::SMEM_BYTES;
+        cfg.stream = stream;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        TimedLaunch timer("scan_mma", stream);
+        if (cudaLaunchKernelEx(&cfg, scan_mma_kernel<2, true>, dummy, dummy, a,
+                               static_cast<const MmaMulti*>(P->table)) != cudaSuccess)
+            return EVP_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
+    return launch_final_merge_multi(P->fm, P->nb, P->total_q, P->fm_smem, stream);
+}
+
+void mma_multi_destroy(MmaMultiPlan* P) {
+    if (!P) return;
+    if (P->table) cudaFree(P->table);
+    if (P->prep) cudaFree(P->prep);
+    if (P->fm) cudaFree(P->fm);
+    delete P;
 }
 
 }  // namespace evp

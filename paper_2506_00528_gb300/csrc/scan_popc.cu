@@ -410,13 +410,14 @@ __device__ __forceinline__ int upper_bound_u64(const uint64_t* a, int n, uint64_
     return lo;
 }
 
-__global__ void __launch_bounds__(FM_THREADS)
-final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
-                   const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
-                   const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k,
-                   int key_bits, int stage_lists, int bin_shift, int dist_bias,
-                   int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
-    extern __shared__ __align__(1024) uint8_t smem[];
+// The merge of one query q (one CTA): lists [q][nslices][2][k] with meta,
+// the scan's threshold tau[q] and histogram hist[q] (either may be absent).
+__device__ __forceinline__ void final_merge_query(
+    const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
+    const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
+    const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k, int key_bits,
+    int stage_lists, int bin_shift, int dist_bias, int64_t* __restrict__ ids,
+    int32_t* __restrict__ dist, const int64_t q, uint8_t* smem) {
     __shared__ int red[FM_THREADS / 32];
     __shared__ int total_s;
     uint64_t* out = reinterpret_cast<uint64_t*>(smem);           // sort buffer
@@ -424,7 +425,6 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
     int* offs = lens + FM_MAX_SLICES;                            // nslices
     uint64_t* staged = reinterpret_cast<uint64_t*>(smem + FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t q = blockIdx.x;
     const int64_t qbase = q * nslices;
 
     // Lengths and buffer indices are clamped to the list storage: after a
@@ -560,6 +560,34 @@ final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict
     }
 }
 
+__global__ void __launch_bounds__(FM_THREADS)
+final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
+                   const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
+                   const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k,
+                   int key_bits, int stage_lists, int bin_shift, int dist_bias,
+                   int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    final_merge_query(lists, meta, tau, hist, minhalf, hist_bins, nslices, k, key_bits,
+                      stage_lists, bin_shift, dist_bias, ids, dist, (int64_t)blockIdx.x, smem);
+}
+
+// Several batches in one launch: CTA i merges query i - q0[b] of the batch b
+// with q0[b] <= i < q0[b + 1].
+__global__ void __launch_bounds__(FM_THREADS)
+final_merge_multi_kernel(const FmBatch* __restrict__ tab, int nb, int key_bits) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int64_t i = blockIdx.x;
+    int lo = 0, hi = nb - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].q0 <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    const FmBatch& b = tab[lo];
+    final_merge_query(b.lists, b.meta, b.tau, b.hist, b.minhalf, b.hist_bins, b.nslices, b.k,
+                      key_bits, b.stage, -1, 0, b.ids, b.dist, i - b.q0, smem);
+}
+
 int choose_stages(int W, int qb) {
     for (int st = MAX_STAGES; st >= 2; --st)
         if (smem_layout(W, st, qb).total <= (size_t)SMEM_BUDGET) return st;
@@ -624,6 +652,23 @@ __global__ void pack_lists_kernel(const int64_t* __restrict__ ids, const int32_t
         meta[(q * nlists + s) * 2] = len;
         meta[(q * nlists + s) * 2 + 1] = 0;
     }
+}
+
+size_t final_merge_smem(int nslices, int k, int* stage) {
+    const size_t list_bytes = (size_t)nslices * k * 8;
+    *stage = list_bytes <= (size_t)FM_STAGE_BYTES ? 1 : 0;
+    return FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4 + (*stage ? list_bytes : 0);
+}
+
+int32_t launch_final_merge_multi(const FmBatch* tab, int nb, int64_t total_q, size_t smem,
+                                 cudaStream_t stream) {
+    if (total_q <= 0) return EVP_OK;
+    if (cudaFuncSetAttribute(final_merge_multi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4 + FM_STAGE_BYTES) != cudaSuccess)
+        return EVP_ERR_CUDA;
+    TimedLaunch timer("final_merge", stream);
+    final_merge_multi_kernel<<<(unsigned)total_q, FM_THREADS, smem, stream>>>(tab, nb, 32 + 13);
+    return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,

@@ -87,6 +87,10 @@ SIGNATURES = {
     "evp_autotune": (_i32, [_p, _i64, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float),
                             ctypes.POINTER(ctypes.c_float), _p]),
     "evp_autotune_clear": (_i32, []),
+    "evp_autotune_save": (_i32, [ctypes.c_char_p]),
+    "evp_autotune_load": (_i32, [ctypes.c_char_p]),
+    "evp_batch_plan_fused": (_i32, [_p]),
+    "evp_batch_plan_tile": (_i32, [_p, _i32]),
     "evp_batch_plan_create": (_i32, [_p, _i32, _i32, _p, ctypes.POINTER(_p)]),
     "evp_batch_plan_path": (_i32, [_p, _i32]),
     "evp_batch_plan_workspace": (_sz, [_p]),
@@ -570,13 +574,22 @@ def autotune(db: "Database", nq: int, k: int, measure: bool = False, stream=None
     return int(path.value), (pm.value if measure else None), (mm.value if measure else None)
 
 
+def autotune_save(path: str):
+    _check(load().evp_autotune_save(path.encode()), "evp_autotune_save")
+
+
+def autotune_load(path: str):
+    _check(load().evp_autotune_load(path.encode()), "evp_autotune_load")
+
+
 class BatchPlan:
     """evp_batch_plan_*: a list of search / kNN batches planned once and run
     (optionally as one captured CUDA graph).  Each item of `batches` is a dict
     with db, and either Q (float32 [nq, d]) + n_shortlist + k (search) or Qc
     (packed codes) + k (kNN); outputs are allocated here."""
 
-    def __init__(self, batches, graph: bool = True, tune: bool = True, stream=None):
+    def __init__(self, batches, graph: bool = True, tune: bool = True, stream=None,
+                 fused: bool = True):
         self.items = []
         descs = (BatchDesc * len(batches))()
         for i, b in enumerate(batches):
@@ -601,7 +614,7 @@ class BatchPlan:
                                      _ptr(dist))
                 self.items.append((Qc, ids, dist))
         self.dbs = [b["db"] for b in batches]
-        flags = (1 if graph else 0) | (0 if tune else 2)
+        flags = (1 if graph else 0) | (0 if tune else 2) | (0 if fused else 4)
         h = ctypes.c_void_p()
         _check(load().evp_batch_plan_create(descs, len(batches), flags, _stream_handle(stream),
                                             ctypes.byref(h)), "evp_batch_plan_create")
@@ -610,6 +623,14 @@ class BatchPlan:
 
     def path(self, i: int) -> int:
         return int(load().evp_batch_plan_path(self.handle, int(i)))
+
+    @property
+    def fused(self) -> int:
+        """Batches scanned by the fused launch."""
+        return int(load().evp_batch_plan_fused(self.handle))
+
+    def tile(self, i: int) -> int:
+        return int(load().evp_batch_plan_tile(self.handle, int(i)))
 
     def run(self, status=None, stream=None):
         _check(load().evp_batch_run(self.handle, _ptr(status), _stream_handle(stream)),

@@ -1,10 +1,15 @@
 """Batched form: uneven batches against three resident databases, planned
 once (autotuned paths), run eagerly and as a captured CUDA graph; every
-batch equals its own evp_db_search / evp_db_knn call."""
+batch equals its own evp_db_search / evp_db_knn call, the fused multi-batch
+tensor-core scan equals the batches run separately, and every batch agrees
+with the oracle (exhaustive kNN by Delta; float64 rerank of the shortlist)."""
+import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2506_00528_gb300 import synth
+from test_gpu_rerank import check_rerank
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +54,7 @@ def test_batch_plan_matches_per_batch_calls(evp_lib, dev, dbs, graph, tune):
     stream = torch.cuda.Stream()
     plan = evp_lib.BatchPlan(spec, graph=graph, tune=tune, stream=stream)
     for i in range(len(spec)):
-        assert plan.path(i) in ((1, 2) if tune else (0,))
+        assert plan.path(i) in ((1, 2, 3) if tune else (0,))
     st = evp_lib.new_status(dev)
     with torch.cuda.stream(stream):
         plan.run(status=st, stream=stream)     # capture (graph) or eager
@@ -75,8 +80,74 @@ def test_autotune_caches_and_reports(evp_lib, dbs):
     db = dbs[1][0]
     evp_lib.load().evp_autotune_clear()
     path, pm, mm = evp_lib.autotune(db, 256, 10, measure=True)
-    assert path in (1, 2) and pm > 0 and mm > 0
-    assert path == (2 if mm < pm else 1)
+    assert path in (1, 2, 3) and pm > 0 and mm > 0
+    assert (path == 1) == (pm <= mm)
     assert evp_lib.autotune(db, 200, 10)[0] == path     # same bucket -> cached
     path_big_k, pm2, mm2 = evp_lib.autotune(db, 40, 500, measure=True)
-    assert path_big_k == (2 if mm2 < pm2 else 1)
+    assert (path_big_k == 1) == (pm2 <= mm2)
+
+
+def _oracle_check(spec, dbs, outs):
+    hosts = {id(db): (U.cpu().numpy(), x) for db, U, d, x in dbs}
+    for b, (ids, second) in zip(spec, outs):
+        U, x = hosts[id(b["db"])]
+        V = oracle.encode(U, x)
+        if "Q" in b:
+            Q = b["Q"].cpu().numpy()
+            sl, _ = oracle.knn(oracle.encode(Q, x), V, b["n_shortlist"])
+            check_rerank(ids.cpu().numpy(), second.cpu().numpy(), Q, U, sl, b["k"])
+        else:
+            d = U.shape[1]
+            Vq, bad = oracle.unpack(b["Qc"].cpu().numpy().view(np.uint64), d)
+            assert bad == 0
+            oi, od = oracle.knn(Vq, V, b["k"])
+            np.testing.assert_array_equal(ids.cpu().numpy(), oi)
+            np.testing.assert_array_equal(second.cpu().numpy(), od)
+
+
+@pytest.mark.parametrize("graph,tune", [(True, False), (False, False), (True, True)])
+def test_fused_plan_matches_separate_and_oracle(evp_lib, dev, dbs, graph, tune):
+    spec = _batches(evp_lib, dbs, dev)
+    stream = torch.cuda.Stream()
+    fused = evp_lib.BatchPlan(spec, graph=graph, tune=tune, fused=True, stream=stream)
+    sep = evp_lib.BatchPlan(spec, graph=False, tune=tune, fused=False, stream=stream)
+    assert sep.fused == 0
+    if not tune:
+        assert fused.fused == 6          # the batches the automatic rule gives the e4m3 scan
+    st = evp_lib.new_status(dev)
+    with torch.cuda.stream(stream):
+        fused.run(status=st, stream=stream)
+        sep.run(status=st, stream=stream)
+    stream.synchronize()
+    for o in fused.outputs(0):
+        o.fill_(-9)
+    with torch.cuda.stream(stream):
+        fused.run(status=st, stream=stream)   # replay (graph) or second eager run
+    stream.synchronize()
+    assert int(st.item()) == 0
+    outs = []
+    for i in range(len(spec)):
+        a, b = fused.outputs(i), sep.outputs(i)
+        assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1]), i
+        assert (fused.tile(i) > 0) == (i in [j for j in range(len(spec)) if fused.tile(j) > 0])
+        outs.append(a)
+    _oracle_check(spec, dbs, outs)
+    fused.close()
+    sep.close()
+
+
+def test_autotune_table_save_and_load(evp_lib, dbs, tmp_path):
+    db = dbs[0][0]
+    evp_lib.load().evp_autotune_clear()
+    path, _, _ = evp_lib.autotune(db, 100, 10, measure=True)
+    f = str(tmp_path / "tune.txt")
+    evp_lib.autotune_save(f)
+    lines = [l for l in open(f) if not l.startswith("#")]
+    assert any("|path|384|128|128|10|" in l for l in lines), lines
+    evp_lib.load().evp_autotune_clear()
+    evp_lib.autotune_load(f)
+    assert evp_lib.autotune(db, 100, 10)[0] == path
+    with open(f, "a") as fh:
+        fh.write("not a line\n")
+    with pytest.raises(evp_lib.EvpError):
+        evp_lib.autotune_load(f)
