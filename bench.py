@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--no-recall", action="store_true")
     ap.add_argument("--no-probe", action="store_true",
                     help="skip the tensor-core rate probe (roofline then uses 2 x bf16)")
-    ap.add_argument("--path", type=int, default=0, help="0 auto, 1 popcount, 2 tensor core, 3 packed tensor core")
+    ap.add_argument("--path", type=int, default=0,
+                    help="0 auto, 1 popcount, 2 tensor core, 3 packed tensor core, "
+                         "4 int8 queries (asymmetric scan), 5 sparse codes (small x)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-form and served-form measurements")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
@@ -276,8 +278,11 @@ def measure_batched(evp, synth, dev, seed_batches=64):
     """Batched form: three resident databases (1M x 384 at x = 128, 4M x 768
     at x = 256, 2M x 1024 at x = 384), 64 kNN batches with sizes
     round(logU[1, 8192]) and k in {10, 100}, each against a database drawn
-    at random; one captured graph (autotuned paths) vs one plain launch per
-    batch (automatic path) on the same inputs."""
+    at random.  Timed four ways on the same inputs: the plan with its fused
+    tensor-core scan (one persistent launch over every e4m3-path batch)
+    replayed as a CUDA graph, the same plan run eagerly, a plan of separate
+    per-batch calls replayed as a graph, and one plain evp_db_knn call per
+    batch (automatic path); the results of all four must be identical."""
     import torch
     rng = np.random.default_rng(20250601)
     shapes = [(1_000_000, 384, 128), (4_000_000, 768, 256), (2_000_000, 1024, 384)]
@@ -297,24 +302,39 @@ def measure_batched(evp, synth, dev, seed_batches=64):
                                 stream=100 + i, device=dev)
         spec.append({"db": db, "Qc": evp.encode(Q, x), "k": int(ks[i])})
     stream = torch.cuda.Stream(dev)
-    plan = evp.BatchPlan(spec, graph=True, tune=True, stream=stream)
-    with torch.cuda.stream(stream):
-        plan.run(stream=stream)          # capture + first run
-        plan.run(stream=stream)
-    stream.synchronize()
+    reps = 3
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    reps = 3
-    with torch.cuda.stream(stream):
-        e0.record(stream)
-        for _ in range(reps):
+
+    def time_plan(plan):
+        with torch.cuda.stream(stream):
+            plan.run(stream=stream)          # capture (graph) + first run
             plan.run(stream=stream)
-        e1.record(stream)
-    stream.synchronize()
-    graph_ms = e0.elapsed_time(e1) / reps
-    outs = [tuple(t.clone() for t in plan.outputs(i)) for i in range(len(spec))]
-    # plain: one evp_db_knn launch per batch, automatic path
-    ws = {}
+            e0.record(stream)
+            for _ in range(reps):
+                plan.run(stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    t0 = time.perf_counter()
+    fused = evp.BatchPlan(spec, graph=True, tune=True, fused=True, stream=stream)
+    tune_s = time.perf_counter() - t0
+    fused_ms = time_plan(fused)
+    outs = [tuple(t.clone() for t in fused.outputs(i)) for i in range(len(spec))]
+    paths = [fused.path(i) for i in range(len(spec))]
+    tiles = sorted({fused.tile(i) for i in range(len(spec)) if fused.tile(i) > 0})
+    n_fused = fused.fused
+    fused.close()
+    eager = evp.BatchPlan(spec, graph=False, tune=True, fused=True, stream=stream)
+    eager_ms = time_plan(eager)
+    eager.close()
+    sep = evp.BatchPlan(spec, graph=True, tune=True, fused=False, stream=stream)
+    sep_ms = time_plan(sep)
+    same = all(torch.equal(o[0], g[0]) and torch.equal(o[1], g[1])
+               for o, g in zip(outs, (sep.outputs(i) for i in range(len(spec)))))
+    sep.close()
+    # plain: one evp_db_knn call per batch on one stream, automatic path
     plain_out = [None] * len(spec)
 
     def plain():
@@ -329,21 +349,23 @@ def measure_batched(evp, synth, dev, seed_batches=64):
         e1.record(stream)
     stream.synchronize()
     plain_ms = e0.elapsed_time(e1) / reps
-    same = all(torch.equal(o[0], p[0]) and torch.equal(o[1], p[1]) for o, p in zip(outs, plain_out))
+    same = same and all(torch.equal(o[0], p_[0]) and torch.equal(o[1], p_[1])
+                        for o, p_ in zip(outs, plain_out))
     total_q = int(sizes.sum())
-    paths = [plan.path(i) for i in range(len(spec))]
-    plan.close()
     for db, *_ in dbs:
         db.close()
-    del ws
+    qps = lambda ms: total_q / (ms / 1e3)
     return {"batches": seed_batches, "queries": total_q,
-            "graph_qps": total_q / (graph_ms / 1e3), "graph_ms": graph_ms,
-            "plain_qps": total_q / (plain_ms / 1e3), "plain_ms": plain_ms,
+            "fused_graph_qps": qps(fused_ms), "fused_graph_ms": fused_ms,
+            "fused_eager_qps": qps(eager_ms), "separate_graph_qps": qps(sep_ms),
+            "plain_qps": qps(plain_ms), "plain_ms": plain_ms,
+            "fused_batches": n_fused, "fused_tiles_per_item": tiles, "plan_and_tune_s": tune_s,
             "paths": {"popc": paths.count(1), "mma": paths.count(2),
                       "mma_packed": paths.count(3)},
             "identical_results": bool(same),
             "workload": "3 DBs (1Mx384 x128, 4Mx768 x256, 2Mx1024 x384), 64 kNN batches "
-                        "logU[1,8192] queries, k in {10,100}"}
+                        "logU[1,8192] queries, k in {10,100}; fused = one persistent "
+                        "tensor-core launch for every e4m3-path batch"}
 
 
 def _request_stream(rate, seconds, seed):
@@ -652,15 +674,23 @@ def main():
     Qall = synth.mixture_torch(pool * B, d, n_centres=a.centres, anisotropic=True,
                                stream=synth.STREAM_QUERIES + 10 * rank, device=dev)
     Qb = [Qall[i * B:(i + 1) * B] for i in range(pool)]
-    db = evp.Database(S, U, d, x, tensor_copy=(a.path not in (1, 3)))
+    db = evp.Database(S, U, d, x, tensor_copy=(a.path in (0, 2)))
     Tq = torch.empty((B, 2 * W), dtype=torch.int64, device=dev)
     sl = torch.empty((B, n_sl), dtype=torch.int64, device=dev)
     sd = torch.empty((B, n_sl), dtype=torch.int32, device=dev)
     rid = torch.empty((B, k), dtype=torch.int64, device=dev)
     rsc = torch.empty((B, k), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
+    Q8 = torch.empty((B, d), dtype=torch.int8, device=dev)
     if a.path == 0:
         ws = torch.empty(db.search_workspace_bytes(B, n_sl, k), dtype=torch.uint8, device=dev)
+    elif a.path == 4:   # int8 queries: the asymmetric tensor-core scan
+        ws = torch.empty(int(evp.load().ternary_knn_i8q_workspace(B, n, d, n_sl)),
+                         dtype=torch.uint8, device=dev)
+    elif a.path == 5:   # sparse database codes
+        E = evp.pack_sparse(S, d, x, status=st)
+        ws = torch.empty(int(evp.load().ternary_knn_sparse_workspace(B, n, d, x, n_sl)),
+                         dtype=torch.uint8, device=dev)
     else:
         ws = torch.empty(int(evp.load().evp_db_knn_workspace(db.handle, B, n_sl, a.path)),
                          dtype=torch.uint8, device=dev)
@@ -668,6 +698,16 @@ def main():
     def step(Q):
         if a.path == 0:   # one C-ABI call: encode -> scan -> rerank
             db.search(Q, n_sl, k, ids=rid, scores=rsc, ws=ws, status=st, stream=stream)
+        elif a.path == 4:  # quantize -> asymmetric scan (masked-addition score) -> rerank
+            evp.quantize_i8(Q, out=Q8, status=st, stream=stream)
+            evp.ternary_knn_i8q(Q8, S, d, x, n_sl, ids=sl, score=sd, ws=ws, status=st,
+                                stream=stream)
+            evp.rerank(Q, U, sl, k, ids=rid, scores=rsc, status=st, stream=stream)
+        elif a.path == 5:  # encode -> scan of the sparse codes -> rerank
+            evp.encode(Q, x, out=Tq, status=st, stream=stream)
+            evp.ternary_knn_sparse(Tq, E, d, x, n_sl, ids=sl, dist=sd, ws=ws, status=st,
+                                   stream=stream)
+            evp.rerank(Q, U, sl, k, ids=rid, scores=rsc, status=st, stream=stream)
         else:             # the same three steps with the scan path forced
             evp.encode(Q, x, out=Tq, status=st, stream=stream)
             db.knn(Tq, n_sl, ids=sl, dist=sd, ws=ws, status=st, stream=stream, path=a.path)
@@ -712,8 +752,8 @@ def main():
     torch.cuda.synchronize()
     evp.timing_enable(False)
     per_kernel = {name: evp.timing_read(name) for name in
-                  ("encode", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
-                   "scan_mma_packed", "final_merge", "rerank")}
+                  ("encode", "quantize", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
+                   "scan_mma_packed", "scan_i8q", "scan_sparse", "final_merge", "rerank")}
     evp.check_status(st, "timed kernels")
 
     # ---- end to end through the API with host buffers (pinned)
@@ -764,7 +804,31 @@ def main():
     n_mma, mma_ms = per_kernel["scan_mma"]
     n_scan, scan_ms = per_kernel["scan_popc"]
     n_pk, pk_ms = per_kernel["scan_mma_packed"]
-    if pk_ms > max(mma_ms, scan_ms):
+    n_iq, iq_ms = per_kernel["scan_i8q"]
+    n_sp, sp_ms = per_kernel["scan_sparse"]
+    if iq_ms > 0 or sp_ms > 0:
+        # asymmetric scan: one launch per <= 32 int8 queries reads the packed
+        # codes (16 W bytes per row); sparse scan: one launch per <= 4
+        # queries reads the sparse codes (2 x bytes per row)
+        name, cnt, tot = ("scan_i8q", n_iq, iq_ms) if iq_ms > 0 else ("scan_sparse", n_sp, sp_ms)
+        avg = tot / max(1, cnt)
+        per_row = 16 * W if iq_ms > 0 else 2 * x
+        gbs = float(n) * per_row / (avg / 1e3) / 1e9
+        roofline = {"kernel": name, "bound": "hbm", "achieved": gbs, "peak": hbm_peak,
+                    "unit": "GB/s", "frac": gbs / hbm_peak, "traffic": None,
+                    "peak_source": f"HBM {hbm_peak} GB/s ({peak_src})", "launches": cnt,
+                    "avg_ms": avg, "bytes_per_row_per_launch": per_row,
+                    "queries_per_launch": 32 if iq_ms > 0 else 4}
+        if iq_ms > 0 and tpeak:
+            # two MMAs per K step (the query's hi and lo parts) per 128-row tile
+            cyc = tpeak["f8_m128_n64" if B > 16 else "f8_m128_n16"]["cycles_per_mma"]
+            mmas = float((n + 127) // 128) * 4 * W
+            mhz = clocks.get("sm_mhz") or 2070.0
+            roofline["mma_instruction_floor_ms"] = mmas * cyc / sm_count / (mhz * 1e6) * 1e3
+            roofline["frac_of_mma_instruction_floor"] = roofline["mma_instruction_floor_ms"] / avg
+        dtype = ("int8 query x e4m3 split (16 hi + lo) -> f32 tensor-core scan (exact)"
+                 if iq_ms > 0 else "uint16 sparse codes, byte-packed table lookups -> int32 Delta")
+    elif pk_ms > max(mma_ms, scan_ms):
         # packed tensor-core scan: one launch per <= 64 queries reads the
         # packed codes (16 W bytes per row) once; 2 d flops per (query, row).
         # Its instruction shape (M = 128, N <= 64) has a fixed cost per MMA,
@@ -865,6 +929,10 @@ def main():
         tern_ids, _ = db.knn(evp.encode(Qr, x), k)
         recall = {"queries": B, "x": x, "rerank_10_at_100": rec(got_rr, truth),
                   "ternary_10_at_10": rec(tern_ids.cpu().numpy(), truth), "per_x": {}}
+        if a.path == 4:
+            # the asymmetric ranking itself (int8 queries against the codes)
+            a_ids, _ = evp.ternary_knn_i8q(evp.quantize_i8(Qr), S, d, x, k)
+            recall["asymmetric_10_at_10"] = rec(a_ids.cpu().numpy(), truth)
         for xx in (64, 256, 384, x):
             Tx = evp.encode(U, xx)
             dbx = evp.Database(Tx, U, d, xx)
