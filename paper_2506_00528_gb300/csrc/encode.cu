@@ -4,8 +4,9 @@
 // One warp per row.  Lane l holds elements j = l + 32 t (t < VPL), so one
 // warp load instruction covers 128 contiguous bytes of the row and, for a
 // fixed t, the 32 lanes hold exactly the 32-bit half-word t of each plane:
-// a warp ballot packs it with no shuffles.  Each warp loads its next row
-// into registers while it works on the current one.
+// two warp ballots (selected, negative) give it with no shuffles; lane 0
+// stages the ballots in shared memory and lane w assembles words w of v+
+// and v-.
 //
 // Selection of the x largest |u_i|.  Magnitudes order exactly by their
 // 31-bit key (float bits with the sign cleared), and for finite values the
@@ -40,14 +41,14 @@ namespace {
 constexpr int ENC_THREADS = 256;
 constexpr int ENC_WARPS = ENC_THREADS / 32;
 constexpr unsigned FULL = 0xffffffffu;
-constexpr float ENC_EPS = 0.15f;      // half-width of the bracket, relative to the estimate
+constexpr float ENC_EPS = 0.18f;      // half-width of the bracket, relative to the estimate
 constexpr float ENC_EMA = 0.25f;      // weight of the newest threshold in the estimate
 
-// Per-warp shared memory: VPL x 32 column words, 32 histogram bins and a
-// 32-slot gather buffer.
+// Per-warp shared memory: VPL x 32 column words, 32 histogram bins, a
+// 32-slot gather buffer and 2 VPL ballot words.
 template <int VPL>
 struct EncSmem {
-    static constexpr int WORDS = VPL * 32 + 64;
+    static constexpr int WORDS = VPL * 32 + 64 + 2 * VPL;
 };
 
 // Number of this warp's elements with |u| >= v (v a finite magnitude or +inf;
@@ -76,6 +77,7 @@ encode_kernel(const float* __restrict__ U, int64_t n, int d, int x, int W,
     uint32_t* col = wsm + lane;        // this lane's column: word j at col[32 j]
     uint32_t* hist = wsm + VPL * 32;   // [32] bins of the bracket
     uint32_t* fin = hist + 32;         // [32] keys of the bin holding tau
+    uint32_t* bal = fin + 32;          // [2 VPL] ballots: selected, then negative
     const float pad = __int_as_float(0x7fffffff);  // NaN: never counted, never selected
 
     auto load_row = [&](int64_t row, float (&v)[VPL]) {
@@ -196,7 +198,6 @@ encode_kernel(const float* __restrict__ U, int64_t n, int d, int x, int W,
 
         // selection and packing
         const bool all_eq = need >= eqn;  // every key equal to tau is taken
-        uint64_t wp = 0, wn = 0;          // this lane's output words (lane < W)
         int base = 0;
 #pragma unroll
         for (int t = 0; t < VPL; ++t) {
@@ -211,27 +212,33 @@ encode_kernel(const float* __restrict__ U, int64_t n, int d, int x, int W,
                 base += __popc(bm);
                 sel = m > tf || (eq && rank < need);
             }
-            const bool ng = u[t] < 0.f;  // -0.0 counts as +1
-            const unsigned bp = __ballot_sync(FULL, sel && !ng);
-            const unsigned bn = __ballot_sync(FULL, sel && ng);
-            if (lane == (t >> 1)) {
-                const int sh = (t & 1) * 32;
-                wp |= (uint64_t)bp << sh;
-                wn |= (uint64_t)bn << sh;
+            const unsigned bs = __ballot_sync(FULL, sel);
+            const unsigned bg = __ballot_sync(FULL, u[t] < 0.f);  // -0.0 counts as +1
+            if (lane == 0) {
+                bal[t] = bs;
+                bal[VPL + t] = bg;
             }
         }
-        uint64_t* out = T + row * (int64_t)(2 * W);
+        __syncwarp();
         if (lane < W) {
-            out[lane] = wp;
-            out[W + lane] = wn;
+            const uint32_t s0 = bal[2 * lane], g0 = bal[VPL + 2 * lane];
+            const uint32_t s1 = 2 * lane + 1 < VPL ? bal[2 * lane + 1] : 0u;
+            const uint32_t g1 = 2 * lane + 1 < VPL ? bal[VPL + 2 * lane + 1] : 0u;
+            const uint64_t sel = ((uint64_t)s1 << 32) | s0, neg = ((uint64_t)g1 << 32) | g0;
+            uint64_t* out = T + row * (int64_t)(2 * W);
+            out[lane] = sel & ~neg;
+            out[W + lane] = sel & neg;
         }
+        __syncwarp();  // bal is rewritten by the next row
     }
 }
 
 template <int VPL, bool EXACT>
 cudaError_t launch_vpl(const float* U, int64_t n, int d, int x, uint64_t* T, int32_t* status,
                        cudaStream_t stream) {
-    constexpr bool PREFETCH = VPL <= 32;
+    // measured: prefetching the next row into registers costs more (register
+    // copies, lower occupancy) than it hides at 24-32 rows in flight per SM
+    constexpr bool PREFETCH = false;
     auto kern = encode_kernel<VPL, EXACT, PREFETCH>;
     const int W = (d + 63) / 64;
     const size_t smem = (size_t)ENC_WARPS * EncSmem<VPL>::WORDS * 4;
