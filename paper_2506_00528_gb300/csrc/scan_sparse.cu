@@ -15,15 +15,19 @@
 // query element q_i in {-1, 0, +1} is held as the bytes
 //   T+[i] = 1 + q_i and T-[i] = 1 - q_i        (both in {0, 1, 2}),
 // the 4 queries of a pass packed into one 32-bit word per (sign, dimension),
-// in 16 lane-interleaved copies in shared memory (word (sign*d + i)*16 + c
-// for lanes c and c + 16) so that the 32 lanes' random lookups rarely meet
-// in a bank.  For a database row s, the sum over its entries of the word for
+// in 16 lane-interleaved copies in shared memory (word (sign*1024 + i)*16 +
+// c for lanes c and c + 16) so that the 32 lanes' random lookups rarely meet
+// in a bank; the table always spans 2 x 1024 dimensions, so an entry's low
+// 10 bits and its sign bit index it directly and a malformed entry still
+// reads inside it.  For a database row s, the sum over its entries of the word for
 // (sign, dimension) is, per byte, A = sum over s's entries of (1 + s_i q_i)
 // = x + <q, s>, so Delta = ||q - s||^2 = 2x - 2 <q, s> = 4x - 2A for codes
 // with x non-zeros each.  Bytes cannot carry: A <= 2x <= 240 (x <= 120).
 // One thread per row reads its row with 16-byte loads straight from
 // global memory (the 16-byte pieces of one row's sectors are merged in
-// flight, so each byte is fetched from HBM once).  Keys (Delta << 32 | row)
+// flight, so each byte is fetched from HBM once), the next tile's row
+// loaded into registers while the current one is scored (the row length is
+// a template parameter), so HBM latency overlaps the work of a tile.  Keys (Delta << 32 | row)
 // below the CTA's threshold for a query go to a candidate buffer; when a
 // buffer may overflow in the next tile, the CTA merges each query's
 // candidates into its sorted top-k list (a block bitonic sort of list and
@@ -48,6 +52,7 @@ constexpr int SP_K_MAX = 256;       // largest k of this path
 constexpr int SP_SORT = 2048;       // bitonic width: list (<= 256) + candidates (<= 1024)
 constexpr int SP_X_MAX = 120;       // bytes of the table sums cannot carry
 constexpr int SP_D_MAX = 1024;
+constexpr int SP_TAB = 2 * SP_D_MAX;  // table words per copy: (sign, dimension)
 
 struct SpArgs {
     const uint64_t* Q;      // this pass's query codes [nqg][2W]
@@ -119,11 +124,13 @@ __device__ __forceinline__ void block_sort(uint64_t* s) {
     }
 }
 
+// NV = x / 8: 16-byte pieces per row.
+template <int NV>
 __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs a) {
     extern __shared__ __align__(16) uint8_t sp_smem[];
     const int d = a.d, x = a.x, k = a.k;
-    uint32_t* tab = reinterpret_cast<uint32_t*>(sp_smem);             // [2][d][SP_COPIES]
-    uint64_t* list = reinterpret_cast<uint64_t*>(sp_smem + (size_t)2 * d * SP_COPIES * 4);
+    uint32_t* tab = reinterpret_cast<uint32_t*>(sp_smem);             // [2][1024][SP_COPIES]
+    uint64_t* list = reinterpret_cast<uint64_t*>(sp_smem + (size_t)SP_TAB * SP_COPIES * 4);
     uint64_t* cand = list + SP_QB * SP_K_MAX;                          // [SP_QB][SP_CAP]
     uint64_t* sortbuf = cand + SP_QB * SP_CAP;                         // [SP_SORT]
     __shared__ uint64_t tau[SP_QB];
@@ -134,13 +141,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
     const int64_t row0 = (int64_t)slice * a.rows_per_slice;
     const int64_t row_end = min(row0 + a.rows_per_slice, a.ns);
 
-    // query tables
-    for (int i = tid; i < 2 * d; i += SP_THREADS) {
-        const int sgn = i >= d, dim = i - sgn * d;
+    // query tables (dimensions >= d hold q = 0)
+    for (int i = tid; i < SP_TAB; i += SP_THREADS) {
+        const int sgn = i >= SP_D_MAX, dim = i - sgn * SP_D_MAX;
         uint32_t v = 0;
         for (int j = 0; j < SP_QB; ++j) {
             int q = 0;
-            if (j < a.nqg) {
+            if (j < a.nqg && dim < d) {
                 const uint64_t* qc = a.Q + (int64_t)j * 2 * a.W;
                 q = (int)((qc[dim >> 6] >> (dim & 63)) & 1ull) -
                     (int)((qc[a.W + (dim >> 6)] >> (dim & 63)) & 1ull);
@@ -157,7 +164,6 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
     }
     __syncthreads();
     const uint32_t* mytab = tab + (tid & (SP_COPIES - 1));
-    const int nvec = x / 8;  // 16-byte pieces per row
 
     // merge each query's candidates into its list (whole block)
     auto merge_all = [&]() {
@@ -189,35 +195,33 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
         }
     };
 
-    for (int64_t t0 = row0; t0 < row_end; t0 += SP_TILE) {
-        const int64_t row = t0 + tid;
+    // entry -> table word: bits 0-9 the dimension, bit 10 the sign
+    auto word_of = [&](uint32_t w) -> uint32_t {
+        const uint32_t lo = (w & 0x3FFu) | ((w >> 5) & 0x400u);
+        const uint32_t hi = ((w >> 16) & 0x3FFu) | ((w >> 21) & 0x400u);
+        return mytab[lo * SP_COPIES] + mytab[hi * SP_COPIES];
+    };
+    uint4 cur[NV], nxt[NV];
+    {
+        const int64_t row = row0 + tid;
         if (row < row_end) {
             const uint4* rp = reinterpret_cast<const uint4*>(a.E + row * x);
+#pragma unroll
+            for (int u = 0; u < NV; ++u) cur[u] = __ldcs(rp + u);
+        }
+    }
+    for (int64_t t0 = row0; t0 < row_end; t0 += SP_TILE) {
+        const int64_t row = t0 + tid, next = row + SP_TILE;
+        if (next < row_end) {  // the next tile's row, in flight while this one is scored
+            const uint4* rp = reinterpret_cast<const uint4*>(a.E + next * x);
+#pragma unroll
+            for (int u = 0; u < NV; ++u) nxt[u] = __ldcs(rp + u);
+        }
+        if (row < row_end) {
             uint32_t acc = 0;
-            for (int v0 = 0; v0 < nvec; v0 += 4) {
-                uint4 w[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (v0 + u < nvec) w[u] = __ldcs(rp + v0 + u);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (v0 + u < nvec) {
-                        const uint32_t h[4] = {w[u].x, w[u].y, w[u].z, w[u].w};
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-#pragma unroll
-                            for (int half = 0; half < 2; ++half) {
-                                const uint32_t ent = (h[e] >> (16 * half)) & 0xFFFFu;
-                                // (sign * d + dim) of the entry
-                                // (clamped: a malformed entry must not read outside the table)
-                                const uint32_t idx =
-                                    min(ent & 0x7FFFu, (uint32_t)(d - 1)) + (ent >> 15) * (uint32_t)d;
-                                acc += mytab[idx * SP_COPIES];
-                            }
-                        }
-                    }
-                }
-            }
+            for (int u = 0; u < NV; ++u)
+                acc += word_of(cur[u].x) + word_of(cur[u].y) + word_of(cur[u].z) + word_of(cur[u].w);
             for (int j = 0; j < a.nqg; ++j) {
                 const uint32_t A = (acc >> (8 * j)) & 0xFFu;
                 const uint64_t key = ((uint64_t)(uint32_t)(4 * x - 2 * (int)A) << 32) | (uint64_t)row;
@@ -227,6 +231,8 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
                 }
             }
         }
+#pragma unroll
+        for (int u = 0; u < NV; ++u) cur[u] = nxt[u];
         __syncthreads();
         // the next tile adds at most SP_TILE candidates per query
         if (tid == 0) {
@@ -275,7 +281,7 @@ SpPlan plan_sparse(int64_t nq, int64_t ns, int d, int k) {
     p.meta_bytes = (lists * 2 * 4 + 255) / 256 * 256;
     p.tau_bytes = ((size_t)std::max<int64_t>(nq, 1) * 8 + 255) / 256 * 256;
     p.ws_bytes = p.list_bytes + p.meta_bytes + p.tau_bytes;
-    p.smem = (size_t)2 * d * SP_COPIES * 4 + (size_t)SP_QB * SP_K_MAX * 8 +
+    p.smem = (size_t)SP_TAB * SP_COPIES * 4 + (size_t)SP_QB * SP_K_MAX * 8 +
              (size_t)SP_QB * SP_CAP * 8 + (size_t)SP_SORT * 8;
     return p;
 }
@@ -321,8 +327,26 @@ int32_t run_sparse_knn(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t
     a.lists = reinterpret_cast<uint64_t*>(w);
     a.meta = reinterpret_cast<int32_t*>(w + p.list_bytes);
     a.tau_global = reinterpret_cast<uint64_t*>(w + p.list_bytes + p.meta_bytes);
-    if (cudaFuncSetAttribute(scan_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)p.smem) != cudaSuccess)
+    void (*kern)(const SpArgs) = nullptr;
+    switch (x / 8) {
+        case 1: kern = scan_sparse_kernel<1>; break;
+        case 2: kern = scan_sparse_kernel<2>; break;
+        case 3: kern = scan_sparse_kernel<3>; break;
+        case 4: kern = scan_sparse_kernel<4>; break;
+        case 5: kern = scan_sparse_kernel<5>; break;
+        case 6: kern = scan_sparse_kernel<6>; break;
+        case 7: kern = scan_sparse_kernel<7>; break;
+        case 8: kern = scan_sparse_kernel<8>; break;
+        case 9: kern = scan_sparse_kernel<9>; break;
+        case 10: kern = scan_sparse_kernel<10>; break;
+        case 11: kern = scan_sparse_kernel<11>; break;
+        case 12: kern = scan_sparse_kernel<12>; break;
+        case 13: kern = scan_sparse_kernel<13>; break;
+        case 14: kern = scan_sparse_kernel<14>; break;
+        default: kern = scan_sparse_kernel<15>; break;
+    }
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
+        cudaSuccess)
         return EVP_ERR_CUDA;
     {
         TimedLaunch timer("scan_init", stream);
@@ -333,7 +357,7 @@ int32_t run_sparse_knn(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t
         a.nqg = (int)std::min<int64_t>(SP_QB, nq - q0);
         a.Q = Q + q0 * 2 * a.W;
         TimedLaunch timer("scan_sparse", stream);
-        scan_sparse_kernel<<<p.nslices, SP_THREADS, p.smem, stream>>>(a);
+        kern<<<p.nslices, SP_THREADS, p.smem, stream>>>(a);
         if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
     }
     return launch_final_merge(a.lists, a.meta, a.tau_global, nullptr, nullptr, 0, nq, p.nslices,
