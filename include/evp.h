@@ -564,6 +564,18 @@ int32_t evp_timing_read(const char* name, int64_t* launches, double* total_ms);
  * multiple of 16 in [16, 256]; 1 <= iters <= 2^26.  kind | 0x100 fills
  * the operands with zeros instead, kind | 0x200 (e4m3 only) with random
  * finite bytes, to show whether the rate depends on the values.
+ * kind | 0x400 (e4m3, n <= 128) takes the A operand from
+ * tensor memory, as the packed scan does; kind | 0x800 (cta_pair = 0)
+ * issues M = 64 instructions.  kind | 0x1000 (e4m3, A in shared memory)
+ * adds a tcgen05.commit after every four instructions, kind | 0x2000 a
+ * test of a completed mbarrier and a tcgen05 fence: the per-stage work of
+ * a pipelined scan's issuing thread; kind | 0x3000 takes every four
+ * instructions' operands from the next of four distinct buffers, as a scan
+ * streaming fresh stages does; kind | 0x4000 switches between two
+ * accumulators every 24 instructions (a scan's tile change); kind | 0x5000
+ * has the other warps read tensor memory throughout (an epilogue);
+ * kind | 0x6000 switches without restarting (accumulate = 1), kind | 0x7000
+ * restarts (accumulate = 0) every 24 instructions without switching.
  * Synchronous: the launch
  * is timed with CUDA events on `stream`.  Outputs: *tflops =
  * 2 M n K iters x instruction issuers / elapsed time; *cycles_per_mma =

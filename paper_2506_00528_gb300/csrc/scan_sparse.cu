@@ -23,11 +23,14 @@
 // (sign, dimension) is, per byte, A = sum over s's entries of (1 + s_i q_i)
 // = x + <q, s>, so Delta = ||q - s||^2 = 2x - 2 <q, s> = 4x - 2A for codes
 // with x non-zeros each.  Bytes cannot carry: A <= 2x <= 240 (x <= 120).
-// One thread per row reads its row with 16-byte loads straight from
-// global memory (the 16-byte pieces of one row's sectors are merged in
-// flight, so each byte is fetched from HBM once), the next tile's row
-// loaded into registers while the current one is scored (the row length is
-// a template parameter), so HBM latency overlaps the work of a tile.  Keys (Delta << 32 | row)
+// Each warp takes 32 consecutive rows per tile and reads them as one
+// contiguous run of 16-byte pieces (lane l takes pieces l, l + 32, ...), so
+// every load instruction is fully coalesced; a lane sums the table words of
+// its pieces' entries, the partial sums go through shared memory (skewed by
+// one word per 32 so that neither side meets in a bank), and lane l adds the
+// x / 8 partial sums of row l.  The next tile's pieces are loaded into
+// registers while the current tile is scored (the row length is a template
+// parameter), so HBM latency overlaps the work of a tile.  Keys (Delta << 32 | row)
 // below the CTA's threshold for a query go to a candidate buffer; when a
 // buffer may overflow in the next tile, the CTA merges each query's
 // candidates into its sorted top-k list (a block bitonic sort of list and
@@ -53,6 +56,9 @@ constexpr int SP_SORT = 2048;       // bitonic width: list (<= 256) + candidates
 constexpr int SP_X_MAX = 120;       // bytes of the table sums cannot carry
 constexpr int SP_D_MAX = 1024;
 constexpr int SP_TAB = 2 * SP_D_MAX;  // table words per copy: (sign, dimension)
+constexpr int SP_NV_MAX = SP_X_MAX / 8;  // 16-byte pieces per row
+constexpr int SP_WARPS = SP_THREADS / 32;
+constexpr int SP_PART = 33 * SP_NV_MAX;  // partial-sum words per warp (skewed)
 
 struct SpArgs {
     const uint64_t* Q;      // this pass's query codes [nqg][2W]
@@ -105,11 +111,12 @@ __global__ void pack_sparse_kernel(const uint64_t* __restrict__ T, int64_t n, in
     }
 }
 
-// Ascending bitonic sort of s[0, SP_SORT) by the whole block.
-__device__ __forceinline__ void block_sort(uint64_t* s) {
-    for (int kk = 2; kk <= SP_SORT; kk <<= 1) {
+// Ascending bitonic sort of s[0, n) by the whole block (n a power of two,
+// at most SP_SORT).
+__device__ __forceinline__ void block_sort(uint64_t* s, int n) {
+    for (int kk = 2; kk <= n; kk <<= 1) {
         for (int j = kk >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < SP_SORT; i += SP_THREADS) {
+            for (int i = threadIdx.x; i < n; i += SP_THREADS) {
                 const int ixj = i ^ j;
                 if (ixj > i) {
                     const uint64_t a = s[i], b = s[ixj];
@@ -133,9 +140,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
     uint64_t* list = reinterpret_cast<uint64_t*>(sp_smem + (size_t)SP_TAB * SP_COPIES * 4);
     uint64_t* cand = list + SP_QB * SP_K_MAX;                          // [SP_QB][SP_CAP]
     uint64_t* sortbuf = cand + SP_QB * SP_CAP;                         // [SP_SORT]
+    uint32_t* part = reinterpret_cast<uint32_t*>(sortbuf + SP_SORT) +
+                     (threadIdx.x >> 5) * SP_PART;                     // this warp's partials
     __shared__ uint64_t tau[SP_QB];
     __shared__ int cnt[SP_QB], len[SP_QB];
-    __shared__ int merge_flag;
     const int tid = threadIdx.x;
     const int slice = blockIdx.x, nslices = gridDim.x;
     const int64_t row0 = (int64_t)slice * a.rows_per_slice;
@@ -169,11 +177,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
     auto merge_all = [&]() {
         for (int j = 0; j < a.nqg; ++j) {
             const int nc = min(cnt[j], SP_CAP), nl = len[j];
-            for (int i = tid; i < SP_SORT; i += SP_THREADS)
+            int n = 2;
+            while (n < nl + nc) n <<= 1;
+            for (int i = tid; i < n; i += SP_THREADS)
                 sortbuf[i] = i < nl ? list[j * SP_K_MAX + i]
                                     : (i < nl + nc ? cand[j * SP_CAP + i - nl] : KEY_NONE);
             __syncthreads();
-            block_sort(sortbuf);
+            block_sort(sortbuf, n);
             const int m = min(nl + nc, k);
             for (int i = tid; i < m; i += SP_THREADS) list[j * SP_K_MAX + i] = sortbuf[i];
             if (tid == 0) {
@@ -201,27 +211,40 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
         const uint32_t hi = ((w >> 16) & 0x3FFu) | ((w >> 21) & 0x400u);
         return mytab[lo * SP_COPIES] + mytab[hi * SP_COPIES];
     };
+    // Warp w scores rows t + 32 w ... t + 32 w + 31 of tile t: pieces
+    // (t + 32 w) * NV + 32 u + lane, u < NV, one coalesced run per warp.
+    const int lane = tid & 31;
+    const uint4* E4 = reinterpret_cast<const uint4*>(a.E);
+    const int64_t piece_end = row_end * NV;
+    auto load_tile = [&](int64_t t, uint4 (&v)[NV]) {
+        const int64_t p0 = (t + (tid - lane)) * NV + lane;
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int64_t g = p0 + 32 * u;
+            v[u] = g < piece_end ? __ldcs(E4 + g) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
     uint4 cur[NV], nxt[NV];
-    {
-        const int64_t row = row0 + tid;
-        if (row < row_end) {
-            const uint4* rp = reinterpret_cast<const uint4*>(a.E + row * x);
-#pragma unroll
-            for (int u = 0; u < NV; ++u) cur[u] = __ldcs(rp + u);
-        }
-    }
+    load_tile(row0, cur);
     for (int64_t t0 = row0; t0 < row_end; t0 += SP_TILE) {
-        const int64_t row = t0 + tid, next = row + SP_TILE;
-        if (next < row_end) {  // the next tile's row, in flight while this one is scored
-            const uint4* rp = reinterpret_cast<const uint4*>(a.E + next * x);
+        if (t0 + SP_TILE < row_end) load_tile(t0 + SP_TILE, nxt);  // in flight meanwhile
+        // other CTAs' thresholds: loaded now, taken at the end of the tile
+        uint64_t tg = KEY_NONE;
+        if (tid < a.nqg) tg = *reinterpret_cast<volatile uint64_t*>(&a.tau_global[a.q0 + tid]);
+        // partial sums of this lane's pieces, then row lane's total
 #pragma unroll
-            for (int u = 0; u < NV; ++u) nxt[u] = __ldcs(rp + u);
+        for (int u = 0; u < NV; ++u)
+            part[33 * u + lane] = word_of(cur[u].x) + word_of(cur[u].y) + word_of(cur[u].z) +
+                                  word_of(cur[u].w);
+        __syncwarp();
+        uint32_t acc = 0;
+#pragma unroll
+        for (int p = 0; p < NV; ++p) {
+            const int g = lane * NV + p;
+            acc += part[g + (g >> 5)];
         }
+        const int64_t row = t0 + tid;
         if (row < row_end) {
-            uint32_t acc = 0;
-#pragma unroll
-            for (int u = 0; u < NV; ++u)
-                acc += word_of(cur[u].x) + word_of(cur[u].y) + word_of(cur[u].z) + word_of(cur[u].w);
             for (int j = 0; j < a.nqg; ++j) {
                 const uint32_t A = (acc >> (8 * j)) & 0xFFu;
                 const uint64_t key = ((uint64_t)(uint32_t)(4 * x - 2 * (int)A) << 32) | (uint64_t)row;
@@ -235,15 +258,10 @@ __global__ void __launch_bounds__(SP_THREADS, 1) scan_sparse_kernel(const SpArgs
         for (int u = 0; u < NV; ++u) cur[u] = nxt[u];
         __syncthreads();
         // the next tile adds at most SP_TILE candidates per query
-        if (tid == 0) {
-            int f = 0;
-            for (int j = 0; j < a.nqg; ++j) f |= cnt[j] > SP_CAP - SP_TILE;
-            merge_flag = f;
-        }
-        __syncthreads();
-        if (merge_flag) merge_all();
-        else if (tid < a.nqg)  // other CTAs' thresholds, now and then
-            tau[tid] = min(tau[tid], *reinterpret_cast<volatile uint64_t*>(&a.tau_global[a.q0 + tid]));
+        bool full = false;
+        for (int j = 0; j < a.nqg; ++j) full |= cnt[j] > SP_CAP - SP_TILE;
+        if (full) merge_all();
+        else if (tid < a.nqg) tau[tid] = min(tau[tid], tg);
         __syncthreads();
     }
     merge_all();
@@ -282,7 +300,8 @@ SpPlan plan_sparse(int64_t nq, int64_t ns, int d, int k) {
     p.tau_bytes = ((size_t)std::max<int64_t>(nq, 1) * 8 + 255) / 256 * 256;
     p.ws_bytes = p.list_bytes + p.meta_bytes + p.tau_bytes;
     p.smem = (size_t)SP_TAB * SP_COPIES * 4 + (size_t)SP_QB * SP_K_MAX * 8 +
-             (size_t)SP_QB * SP_CAP * 8 + (size_t)SP_SORT * 8;
+             (size_t)SP_QB * SP_CAP * 8 + (size_t)SP_SORT * 8 +
+             (size_t)SP_WARPS * SP_PART * 4;
     return p;
 }
 

@@ -369,7 +369,9 @@ def test_stall_producer(path: int, fills: int):
 def probe_tensor_rate(kind: int = 0, cta_pair: bool = False, n: int = 256,
                       iters: int = 1 << 16, stream=None):
     """evp_probe_tensor_rate: (TFLOP/s, SM clocks per instruction, ms) of
-    back-to-back tcgen05.mma (kind 0 = e4m3 f8f6f4, 1 = bf16 f16) on every SM."""
+    back-to-back tcgen05.mma (kind 0 = e4m3 f8f6f4, 1 = bf16 f16) on every SM.
+    kind | 0x100 / 0x200: zero / random operands; | 0x400: A in tensor memory;
+    | 0x800: M = 64."""
     tf, cyc, ms = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
     _check(load().evp_probe_tensor_rate(int(kind), 1 if cta_pair else 0, int(n), int(iters),
                                         ctypes.byref(tf), ctypes.byref(cyc), ctypes.byref(ms),
