@@ -82,26 +82,35 @@ def measure_tensor_peak(evp, sampler_cls, local, seconds=1.0):
     """Measured dense tensor-core rate (evp_probe_tensor_rate) for the
     instruction shapes the scans issue, each run back to back for about
     `seconds` with the SM clocks sampled meanwhile."""
+    import torch
     out = {}
-    shapes = [("f8_pair_m256_n256", 0, True, 256), ("f8_m128_n256", 0, False, 256),
+    shapes = [("f4_pair_m256_n256", 2, True, 256), ("f4_m128_n256", 2, False, 256),
+              ("f8_pair_m256_n256", 0, True, 256), ("f8_m128_n256", 0, False, 256),
               ("bf16_m128_n256", 1, False, 256), ("f8_m128_n64", 0, False, 64),
               ("f8_m128_n16", 0, False, 16)]
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     for name, kind, pair, nn in shapes:
         evp.probe_tensor_rate(kind, pair, nn, 1 << 12)          # warm-up
         sampler = sampler_cls(local)
         sampler.start()
         t_end = time.perf_counter() + (seconds if nn == 256 else 0.25)
         rates, cycles = [], []
+        # long launches (tens of ms), so that launch and set-up time is a
+        # small part of the elapsed time the rate is taken over
+        iters = 1 << 18 if nn == 256 else 1 << 17
         while time.perf_counter() < t_end:
-            tf, cyc, _ = evp.probe_tensor_rate(kind, pair, nn, 1 << 16)
+            tf, cyc, _ = evp.probe_tensor_rate(kind, pair, nn, iters)
             rates.append(tf)
             cycles.append(cyc)
         clk = sampler.stop()
         m = 256 if pair else 128
-        kk = 32 if kind == 0 else 16
+        kk = {0: 32, 1: 16, 2: 64}[kind]
+        fpc = 2.0 * m * nn * kk / float(np.median(cycles)) / (2 if pair else 1)
+        mhz = clk.get("sm_mhz")
         out[name] = {"tflops": float(np.median(rates)), "cycles_per_mma": float(np.median(cycles)),
-                     "flop_per_clk_per_sm": 2.0 * m * nn * kk / float(np.median(cycles)) / (2 if pair else 1),
-                     "launches": len(rates), "sm_mhz": clk.get("sm_mhz"),
+                     "flop_per_clk_per_sm": fpc,
+                     "tflops_at_sampled_clock": fpc * sms * mhz * 1e6 / 1e12 if mhz else None,
+                     "launches": len(rates), "sm_mhz": mhz,
                      "reasons": clk.get("reasons")}
     return out
 
@@ -279,7 +288,7 @@ def measure_batched(evp, synth, dev, seed_batches=64):
     at x = 256, 2M x 1024 at x = 384), 64 kNN batches with sizes
     round(logU[1, 8192]) and k in {10, 100}, each against a database drawn
     at random.  Timed four ways on the same inputs: the plan with its fused
-    tensor-core scan (one persistent launch over every e4m3-path batch)
+    tensor-core scan (one persistent launch over every fp4-path batch)
     replayed as a CUDA graph, the same plan run eagerly, a plan of separate
     per-batch calls replayed as a graph, and one plain evp_db_knn call per
     batch (automatic path); the results of all four must be identical."""
@@ -365,7 +374,7 @@ def measure_batched(evp, synth, dev, seed_batches=64):
             "identical_results": bool(same),
             "workload": "3 DBs (1Mx384 x128, 4Mx768 x256, 2Mx1024 x384), 64 kNN batches "
                         "logU[1,8192] queries, k in {10,100}; fused = one persistent "
-                        "tensor-core launch for every e4m3-path batch"}
+                        "tensor-core launch for every fp4-path batch"}
 
 
 def _request_stream(rate, seconds, seed):
@@ -752,7 +761,7 @@ def main():
     torch.cuda.synchronize()
     evp.timing_enable(False)
     per_kernel = {name: evp.timing_read(name) for name in
-                  ("encode", "quantize", "scan_init", "scan_popc", "unpack_fp8", "scan_mma",
+                  ("encode", "quantize", "scan_init", "scan_popc", "unpack_fp4", "scan_mma",
                    "scan_mma_packed", "scan_i8q", "scan_sparse", "final_merge", "rerank")}
     evp.check_status(st, "timed kernels")
 
@@ -791,15 +800,24 @@ def main():
     hbm_peak, bf16_peak, peak_src = load_peaks()
     tpeak = None if a.no_probe else measure_tensor_peak(evp, ClockSampler, local)
     fp8_2x_bf16 = 2.0 * bf16_peak          # nominal fp8 : bf16 dense ratio 2 : 1
+    fp4_4x_bf16 = 4.0 * bf16_peak          # block-scaled fp4 (mxf4) : bf16, 4 : 1 per clock (probe)
     if tpeak:
         fp8_peak = max(tpeak["f8_pair_m256_n256"]["tflops"], tpeak["f8_m128_n256"]["tflops"])
+        fp4_peak = max(tpeak["f4_pair_m256_n256"]["tflops"], tpeak["f4_m128_n256"]["tflops"])
         fp8_src = (f"fp8 dense measured by evp_probe_tensor_rate on every SM "
                    f"({fp8_peak:.0f} TFLOP/s at {tpeak['f8_pair_m256_n256']['sm_mhz']} MHz); "
                    f"2 x measured bf16 = {fp8_2x_bf16:.0f} beside it; HBM {hbm_peak} GB/s "
                    f"({peak_src})")
+        fp4_src = (f"fp4 (kind::mxf4) dense measured by evp_probe_tensor_rate on every SM "
+                   f"({fp4_peak:.0f} TFLOP/s at {tpeak['f4_pair_m256_n256']['sm_mhz']} MHz); "
+                   f"4 x measured bf16 = {fp4_4x_bf16:.0f} beside it; HBM {hbm_peak} GB/s "
+                   f"({peak_src})")
     else:
         fp8_peak = fp8_2x_bf16
+        fp4_peak = fp4_4x_bf16
         fp8_src = f"fp8 dense = 2 x bf16 {bf16_peak} TFLOP/s ({peak_src}); HBM {hbm_peak} GB/s"
+        fp4_src = (f"fp4 (kind::mxf4) dense = 4 x bf16 {bf16_peak} TFLOP/s ({peak_src}); "
+                   f"HBM {hbm_peak} GB/s")
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     n_mma, mma_ms = per_kernel["scan_mma"]
     n_scan, scan_ms = per_kernel["scan_popc"]
@@ -864,17 +882,17 @@ def main():
         dtype = "e4m3 x e4m3 -> f32 tensor-core scan (exact on -1/0/+1), f32 encode/rerank"
     elif mma_ms >= scan_ms:
         # tensor-core scan: algorithmic flops = 2 d per (query, row) pair; it
-        # reads the database's e4m3 copy (Kp bytes per row) once per launch,
-        # which binds instead for small batches
+        # reads the database's e2m1 copy (Kp bytes per row, two elements a
+        # byte) once per launch, which binds instead for small batches
         avg = mma_ms / max(1, n_mma)
         flops = 2.0 * d * B * n * (a.steps / max(1, n_mma))
-        kp = (d + 127) // 128 * 128
-        e4m3_bytes = float(n) * kp
+        kp = (d + 255) // 256 * 128
+        fp4_bytes = float(n) * kp
         tflops = flops / (avg / 1e3) / 1e12
-        gbs = e4m3_bytes / (avg / 1e3) / 1e9
-        tensor_frac, hbm_frac = tflops / fp8_peak, gbs / hbm_peak
+        gbs = fp4_bytes / (avg / 1e3) / 1e9
+        tensor_frac, hbm_frac = tflops / fp4_peak, gbs / hbm_peak
         if tensor_frac >= hbm_frac:
-            bound = {"bound": "tensor", "achieved": tflops, "peak": fp8_peak, "unit": "TFLOP/s",
+            bound = {"bound": "tensor", "achieved": tflops, "peak": fp4_peak, "unit": "TFLOP/s",
                      "frac": tensor_frac}
         else:
             bound = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -882,11 +900,12 @@ def main():
         roofline = {
             "kernel": "scan_mma", **bound,
             "traffic": measured_traffic("scan_mma", n, d, B, a.shortlist),
-            "tensor_frac": tensor_frac, "hbm_frac": hbm_frac, "e4m3_gbs": gbs,
-            "peak_2x_bf16": fp8_2x_bf16, "frac_vs_2x_bf16": tflops / fp8_2x_bf16,
-            "peak_source": fp8_src, "launches": n_mma, "avg_ms": avg,
+            "tensor_frac": tensor_frac, "hbm_frac": hbm_frac, "fp4_gbs": gbs,
+            "peak_4x_bf16": fp4_4x_bf16, "frac_vs_4x_bf16": tflops / fp4_4x_bf16,
+            "frac_vs_fp8_peak": tflops / fp8_peak,
+            "peak_source": fp4_src, "launches": n_mma, "avg_ms": avg,
         }
-        dtype = "e4m3 x e4m3 -> f32 tensor-core scan (exact on -1/0/+1), f32 encode/rerank"
+        dtype = "e2m1 x e2m1 -> f32 tensor-core scan (kind::mxf4, unit scales; exact on -1/0/+1), f32 encode/rerank"
     else:
         # popcount scan: one pass over the codes per <= 16 queries; per
         # (query, row) pair 4W 32-bit popcounts

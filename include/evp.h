@@ -243,11 +243,12 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
  *   EVP_PATH_POPC  bitplane popcount scan on the integer pipe: reads the
  *                  packed codes once per 16 queries; best for up to three
  *                  queries.
- *   EVP_PATH_MMA   tensor-core scan (tcgen05, e4m3 operands holding -1/0/+1,
- *                  float32 accumulation, exact) with the queries as the
- *                  128-row side: the codes are expanded to one byte per
- *                  element (in the workspace when S is given packed, or
- *                  once for a database created with EVP_DB_TENSOR_COPY).
+ *   EVP_PATH_MMA   tensor-core scan (tcgen05 kind::mxf4: 4-bit e2m1 operands
+ *                  holding -1/0/+1, unit block scales, float32
+ *                  accumulation, exact) with the queries as the 128-row
+ *                  side: the codes are expanded to half a byte per element
+ *                  (in the workspace when S is given packed, or once for a
+ *                  database created with EVP_DB_TENSOR_COPY).
  *                  A 128-query tile serves all 128 queries for k <= 128 and
  *                  fewer (64, 32, 16) for larger k; best for large batches.
  *   EVP_PATH_MMA_PACKED  tensor-core scan with the database as the 128-row
@@ -258,7 +259,7 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
  *                  for medium batches.
  *   EVP_PATH_AUTO  POPC for nq <= EVP_AUTO_POPC_MAX_NQ; MMA_PACKED (where
  *                  supported) up to EVP_AUTO_PACKED_MAX_NQ queries against a
- *                  resident database holding its e4m3 copy, and up to
+ *                  resident database holding its e2m1 copy, and up to
  *                  EVP_AUTO_PACKED_MAX_NQ_NO_COPY otherwise (MMA would first
  *                  expand the database); MMA beyond.  Where the packed path
  *                  does not apply: MMA when nq > 16 (> 8 with a resident
@@ -341,8 +342,8 @@ int32_t rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int32_t d
  * evp_db_create borrows T ([ns][2W] packed codes, device, 16-byte aligned)
  * and U ([ns][d] float32 rows, device, or NULL if no rerank is wanted); the
  * caller keeps both alive and unchanged until evp_db_destroy.  With
- * EVP_DB_TENSOR_COPY the handle also owns a one-byte-per-element e4m3 copy
- * of the codes ([ns][Kp], Kp = d rounded up to 128; allocated with
+ * EVP_DB_TENSOR_COPY the handle also owns a half-byte-per-element e2m1 copy
+ * of the codes ([ns][Kp] bytes, Kp = d/2 rounded up to 128; allocated with
  * cudaMalloc, filled on `stream`, which is synchronised before returning)
  * so that the tensor-core scan need not rebuild it per call.
  * Returns EVP_OK, EVP_ERR_INVALID, EVP_ERR_UNSUPPORTED (d > EVP_MAX_D_SCAN),
@@ -420,7 +421,7 @@ int32_t evp_db_search_host(evp_db_t db, const float* Q_host, int64_t nq, int32_t
  * evp_batch_plan_create checks every descriptor, picks each batch's path
  * with evp_autotune (EVP_BATCH_NO_TUNE: the automatic rule instead) and
  * allocates one workspace region per batch (the plan owns it).  Every batch
- * whose path is the e4m3 tensor-core scan (EVP_PATH_MMA) and whose database
+ * whose path is the fp4 tensor-core scan (EVP_PATH_MMA) and whose database
  * holds its tensor copy (EVP_DB_TENSOR_COPY) joins the fused scan (at most
  * 64 batches): one persistent launch over the work items -- (batch, query
  * unit, database slice) -- of all of them, after one launch that prepares
@@ -556,7 +557,9 @@ int32_t evp_timing_read(const char* name, int64_t* launches, double* total_ms);
  * counterpart).
  *
  * Every SM (kind 0: tcgen05.mma.kind::f8f6f4 with e4m3 operands, K = 32;
- * kind 1: kind::f16 with bf16 operands, K = 16; float32 accumulation)
+ * kind 1: kind::f16 with bf16 operands, K = 16; kind 2: kind::mxf4 with
+ * packed e2m1 operands and unit ue8m0 block scales, K = 64, the ternary
+ * scan's form; float32 accumulation)
  * issues `iters` instructions of shape M x n x K back to back from one
  * thread, on operands resident in shared memory that hold +1, -1 and 0 in
  * equal shares (the values the scans contract).  cta_pair = 0: one CTA per

@@ -4,7 +4,7 @@
 // evp_batch_plan_create validates a list of batch descriptors and picks each
 // batch's scan path from the autotuner (timing the paths on first sight of a
 // (GPU, d, x, query-count bucket, k, row-count bucket) class, see
-// evp_autotune).  Every batch whose path is the e4m3 tensor-core scan and
+// evp_autotune).  Every batch whose path is the fp4 tensor-core scan and
 // whose database holds its tensor copy joins the fused scan: one persistent
 // launch over the work items (query unit, database slice) of all of them,
 // preceded by one launch that prepares every batch's queries and followed by
@@ -34,7 +34,7 @@ namespace {
 constexpr int BRANCHES = 4;               // forked streams inside one run
 // Tile shapes tried for the fused scan, in k-chunk tiles per work item (an
 // item of a batch with kc 128-byte K chunks per row covers shape / kc
-// database tiles of 256 rows); 0 = each batch sliced in whole waves of the
+// database tiles of 240 rows); 0 = each batch sliced in whole waves of the
 // persistent grid, as its own call would be.  Items must stay large: each
 // ends with a sort of its heaps and a k-key list per query, and every
 // list is merged at the end.
@@ -269,7 +269,8 @@ int32_t build_multi(evp_batch_plan* p, int shape) {
         s.ws = w + L.codes + L.sl_ids + L.sl_dist;
         s.tiles_per_item = tiles;
         // reported shape: database tiles per item (whole-wave slices included)
-        p->tiles[i] = (int32_t)(evp::plan_mma_scan(b.nq, s.ns, s.d, s.k, false, tiles).rows_per_slice / 256);
+        p->tiles[i] = (int32_t)(evp::plan_mma_scan(b.nq, s.ns, s.d, s.k, false, tiles).rows_per_slice /
+                                evp::MMA_TILE_ROWS);
         specs.push_back(s);
     }
     p->shape = shape;

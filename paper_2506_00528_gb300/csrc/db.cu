@@ -11,7 +11,7 @@ struct evp_db {
     const float* U;     // borrowed float rows [ns][d] (may be null)
     int64_t ns;
     int d, x, W, kp;
-    uint8_t* S8;        // owned e4m3 copy [ns][kp] (null without EVP_DB_TENSOR_COPY)
+    uint8_t* S8;        // owned e2m1 copy [ns][kp] (null without EVP_DB_TENSOR_COPY)
 };
 
 using namespace evp;
@@ -81,7 +81,7 @@ int32_t evp_db_create(const uint64_t* T, const float* U, int64_t ns, int32_t d, 
         }
         db->S8 = static_cast<uint8_t*>(p);
         cudaStream_t s = static_cast<cudaStream_t>(stream);
-        if (launch_unpack_fp8(T, ns, d, db->S8, s) != cudaSuccess ||
+        if (launch_unpack_fp4(T, ns, d, db->S8, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             cudaFree(db->S8);
             delete db;

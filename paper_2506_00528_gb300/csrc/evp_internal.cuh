@@ -307,7 +307,7 @@ int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int 
                        int32_t* status, cudaStream_t stream);
 
 struct MmaPlan {
-    int kp;                 // K padded to a multiple of 128
+    int kp;                 // bytes per row of the e2m1 operands (a multiple of 128)
     int qa;                 // active queries per 128-row tile
     int qtiles;             // query tiles (of qa queries)
     int nslices;            // database slices per query tile
@@ -318,14 +318,15 @@ struct MmaPlan {
     size_t a_bytes, b_bytes, list_bytes, meta_bytes, tau_bytes, hist_bytes, ws_bytes;
 };
 constexpr int MMA_K_MAX = 1024;  // largest k of the tensor-core path
+constexpr int MMA_TILE_ROWS = 240;  // database rows per tensor-core tile (the MMA's N)
 // Smallest query count for which the automatic choice takes the tensor-core
-// scan: from 9 queries when the database's e4m3 copy is resident (the scan
-// then reads 1 byte per element at HBM speed, faster than a 16-query
+// scan: from 9 queries when the database's e2m1 copy is resident (the scan
+// then reads half a byte per element at HBM speed, faster than a 16-query
 // popcount pass), from 17 when the copy must be built first.
 inline int64_t auto_mma_min_nq(bool resident_copy) { return resident_copy ? 9 : 17; }
 // Largest query count for which the automatic choice takes the packed
 // tensor-core scan (where it applies): one 64-query pass costs about what
-// the e4m3 scan costs against a resident copy; without one, the e4m3 scan
+// the fp4 scan costs against a resident copy; without one, the fp4 scan
 // must first expand the whole database.
 inline int64_t auto_packed_max_nq(bool resident_copy) {
     return resident_copy ? EVP_AUTO_PACKED_MAX_NQ : EVP_AUTO_PACKED_MAX_NQ_NO_COPY;
@@ -335,13 +336,13 @@ int mma_kp(int d);
 // the same other arguments) on `path` (AUTO resolved per call).
 size_t knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert_db);
 int mma_active_queries(int k);
-// tiles_per_item > 0: slices of about that many 256-row database tiles (the
+// tiles_per_item > 0: slices of about that many 240-row database tiles (the
 // tile shape of the fused multi-batch scan) instead of whole waves.
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
                       int tiles_per_item = 0);
 
 // Fused multi-batch tensor-core scan (the batched form): several kNN
-// batches, each against a resident e4m3 database copy, scanned by one
+// batches, each against a resident e2m1 database copy, scanned by one
 // persistent launch over the work items of all of them, then merged by one
 // multi-batch final merge.  The plan owns a small device table (tensor maps,
 // per-batch arguments) written once at creation; workspaces are the
@@ -349,13 +350,13 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
 struct MmaBatchSpec {
     const uint64_t* Q;   // packed query codes [nq][2W]
     int64_t nq;
-    const uint8_t* S8;   // resident e4m3 copy of the database [ns][kp], 256-byte aligned
+    const uint8_t* S8;   // resident e2m1 copy of the database [ns][kp], 256-byte aligned
     int64_t ns;
     int d, x, k;
     int64_t* ids;        // [nq][k]
     int32_t* dist;       // [nq][k]
     void* ws;            // mma_multi_ws(...) bytes, 256-byte aligned
-    int tiles_per_item;  // tile shape: 256-row database tiles per work item
+    int tiles_per_item;  // tile shape: 240-row database tiles per work item
 };
 struct MmaMultiPlan;
 size_t mma_multi_ws(int64_t nq, int64_t ns, int d, int k, int tiles_per_item);
@@ -364,9 +365,9 @@ int32_t mma_multi_run(MmaMultiPlan* p, int32_t* status, cudaStream_t stream);
 void mma_multi_destroy(MmaMultiPlan* p);
 // spread_cg > 0: query rows placed as the tensor-core scan's small-batch
 // spread over spread_cg CTAs expects (queries only).
-cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
+cudaError_t launch_unpack_fp4(const uint64_t* T, int64_t n, int d, uint8_t* out,
                               cudaStream_t stream, int spread_cg = 0);
-// S8: resident e4m3 copy of the database ([ns][kp]) or nullptr, in which case
+// S8: resident e2m1 copy of the database ([ns][kp]) or nullptr, in which case
 // S is converted into the workspace first.
 int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint64_t* S,
                     int64_t ns, int d, int x, int k, int64_t* ids, int32_t* dist, void* ws,
@@ -397,14 +398,14 @@ int32_t run_sparse_knn(const uint64_t* Q, int64_t nq, const uint16_t* E, int64_t
                        int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                        int32_t* status, cudaStream_t stream);
 
-// Internals of a resident database (db.cu): its e4m3 copy (null without
+// Internals of a resident database (db.cu): its e2m1 copy (null without
 // EVP_DB_TENSOR_COPY), its float rows (may be null) and its x.
 const uint8_t* db_tensor_copy(const evp_db* db);
 const float* db_float_rows(const evp_db* db);
 int db_x(const evp_db* db);
 
 // Path the automatic rule takes for nq queries (resident_copy: the
-// database's e4m3 copy is resident).
+// database's e2m1 copy is resident).
 int auto_path(int64_t nq, int64_t ns, int d, int k, bool resident_copy);
 
 cudaError_t launch_rerank(const float* Q, int64_t nq, const float* S, int64_t ns, int d,

@@ -38,7 +38,9 @@ __device__ __forceinline__ void pr_cluster_sync() {
     asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// KIND: 0 = f8f6f4 (e4m3), 1 = f16 (bf16).  CG: CTAs per instruction.
+// KIND: 0 = f8f6f4 (e4m3), 1 = f16 (bf16), 2 = mxf4 (e2m1, K = 64, unit
+// ue8m0 scale factors in TMEM columns 384-415 of the accumulator's base).
+// CG: CTAs per instruction.
 // AMODE 1: A in tensor memory (a = TMEM address), else a shared-memory
 // descriptor.  ACC: accumulate into D (0 for the first instruction).
 template <int CG, int KIND, int AMODE, int ACC>
@@ -54,6 +56,18 @@ __device__ __forceinline__ void pr_mma(uint32_t d, uint64_t a, uint64_t b, uint3
         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                      "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d),
                      "r"((uint32_t)a), "l"(b), "r"(idesc), "n"(ACC)
+                     : "memory");
+    } else if constexpr (KIND == 2 && CG == 1) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X "
+                     "[%0], %1, %2, %3, [%5], [%6], p;\n\t}" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "n"(ACC), "r"(d + 384u), "r"(d + 392u)
+                     : "memory");
+    } else if constexpr (KIND == 2) {
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X "
+                     "[%0], %1, %2, %3, [%5], [%6], p;\n\t}" ::"r"(d),
+                     "l"(a), "l"(b), "r"(idesc), "n"(ACC), "r"(d + 384u), "r"(d + 392u)
                      : "memory");
     } else if constexpr (KIND == 0 && CG == 1) {
         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -134,7 +148,11 @@ probe_mma_kernel(int fill, int64_t iters, uint32_t idesc, int64_t* cycles, int32
         const uint32_t h = (uint32_t)i * 2654435761u + blockIdx.x * 40503u;
         const uint32_t c0 = (h >> 7) % 3u, c1 = (h >> 17) % 3u;
         uint16_t v;
-        if (KIND == 0) {
+        if (KIND == 2) {
+            const uint16_t e[3] = {0x0, 0x2, 0xA};  // 0, +1, -1 in e2m1
+            const uint32_t c2 = (h >> 23) % 3u, c3 = (h >> 27) % 3u;
+            v = (uint16_t)(e[c0] | (e[c1] << 4) | (e[c2] << 8) | (e[c3] << 12));
+        } else if (KIND == 0) {
             const uint8_t e[3] = {0x00, 0x38, 0xB8};  // 0, +1, -1 in e4m3
             v = (uint16_t)(e[c0] | (e[c1] << 8));
         } else {
@@ -171,6 +189,17 @@ probe_mma_kernel(int fill, int64_t iters, uint32_t idesc, int64_t* cycles, int32
     if constexpr (CG == 2) pr_cluster_sync();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (KIND == 2) {  // unit scale factors (ue8m0 0x7F) in columns 384-415 of every lane
+        uint32_t v[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c) v[c] = 0x7F7F7F7Fu;
+        pr_tmem_st32(tmem + ((uint32_t)(warp * 32) << 16) + 384u, v);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
+        __syncthreads();
+        if constexpr (CG == 2) pr_cluster_sync();
+        tc_fence_after();
+    }
     if (AMODE == 1) {  // A: this warp's 32 lanes x 32 columns (four K steps of e4m3 bytes)
         uint32_t v[32];
 #pragma unroll
@@ -319,7 +348,8 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
     const bool tmem_a = (kind >> 10) & 1, m64 = (kind >> 11) & 1;
     const int extra = (kind >> 12) & 7;  // per-four-MMA extra work (see the kernel)
     kind &= 0xff;
-    if ((kind != 0 && kind != 1) || fill == 3 || (fill == 2 && kind != 0) || n < 16 || n > 256 ||
+    if ((kind != 0 && kind != 1 && kind != 2) || fill == 3 || (fill == 2 && kind != 0) || n < 16 ||
+        n > 256 ||
         n % 16 != 0 || iters < 1 || iters > (int64_t(1) << 26) || !tflops || !cycles_per_mma ||
         !ms)
         return EVP_ERR_INVALID;
@@ -327,15 +357,20 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
     if (tmem_a && (m64 || kind != 0 || fill == 2 || n > 128)) return EVP_ERR_INVALID;
     if (m64 && n % 8 != 0) return EVP_ERR_INVALID;
     if (extra != 0 && (tmem_a || kind != 0)) return EVP_ERR_INVALID;
+    if (kind == 2 && (tmem_a || m64 || fill != 0)) return EVP_ERR_INVALID;
     if (extra >= 4 && n > 256) return EVP_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int sms = num_sms();
     const int workers = cg == 2 ? sms / 2 : sms;
     const int m = m64 ? 64 : 128 * cg;
     // D = f32; A, B = e4m3 (format 0) or bf16 (format 1); both K-major.
+    // mxf4: A, B = e2m1 (format 1 of the block-scaled kinds), ue8m0 scales.
     const uint32_t fmt = kind == 0 ? 0u : 1u;
-    const uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) |
-                           ((uint32_t)(m >> 4) << 24);
+    const uint32_t idesc =
+        kind == 2 ? (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | (1u << 23) |
+                        ((uint32_t)(m >> 4) << 24)
+                  : (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(n >> 3) << 17) |
+                        ((uint32_t)(m >> 4) << 24);
     int64_t* cycles = nullptr;
     int32_t* status = nullptr;
     if (cudaMalloc(&cycles, sizeof(int64_t) * workers) != cudaSuccess) return EVP_ERR_NO_MEMORY;
@@ -353,6 +388,7 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
     if (cg == 1) {
         void (*kern)(int, int64_t, uint32_t, int64_t*, int32_t*) =
             tmem_a ? probe_mma_kernel<1, 0, 1, 0>
+                   : kind == 2 ? probe_mma_kernel<1, 2, 0, 0>
                    : (kind == 1 ? probe_mma_kernel<1, 1, 0, 0>
                                 : (extra == 1 ? probe_mma_kernel<1, 0, 0, 1>
                                               : (extra == 2 ? probe_mma_kernel<1, 0, 0, 2>
@@ -373,6 +409,7 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
     } else {
         void (*kern)(int, int64_t, uint32_t, int64_t*, int32_t*) =
             tmem_a ? probe_mma_kernel<2, 0, 1, 0>
+                   : kind == 2 ? probe_mma_kernel<2, 2, 0, 0>
                    : (kind == 1 ? probe_mma_kernel<2, 1, 0, 0>
                                 : (extra == 1 ? probe_mma_kernel<2, 0, 0, 1>
                                               : (extra == 2 ? probe_mma_kernel<2, 0, 0, 2>
@@ -415,7 +452,7 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
         } else {
             double sum = 0.0;
             for (int64_t c : cyc) sum += (double)c;
-            const int kdim = kind == 0 ? 32 : 16;
+            const int kdim = kind == 0 ? 32 : (kind == 2 ? 64 : 16);
             *ms = t;
             *tflops = 2.0 * m * n * kdim * (double)iters4 * workers / (t * 1e-3) / 1e12;
             *cycles_per_mma = sum / workers / (double)iters4;

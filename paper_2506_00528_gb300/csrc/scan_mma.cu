@@ -1,25 +1,31 @@
 // ternary_knn, tensor-core path: the exhaustive scan as a dense contraction
-// on the 5th-generation tensor cores (tcgen05, kind::f8f6f4).
+// on the 5th-generation tensor cores (tcgen05, kind::mxf4).
 //
 // b2sp(q, s) of Sec. 5.1.2 is the scalar product of two ternary vectors.
-// Both operands are written as e4m3 bytes (+1 = 0x38, -1 = 0xB8, 0 = 0x00),
-// which represent {-1, 0, 1} exactly; the tensor core accumulates in
-// float32, where every partial sum is an integer of magnitude <= d < 2^24,
-// so D = Q S^T holds b2sp exactly.  Delta = 2x - 2 b2sp for codes with x
-// non-zeros each.  Float8 is used instead of int8 because the dense int8
-// tensor rate of this GPU generation is far below its fp8 rate.
+// Both operands are written as 4-bit e2m1 values (+1 = 0x2, -1 = 0xA, 0 =
+// 0x0, two per byte, the lower K index in the low nibble), which represent
+// {-1, 0, 1} exactly; the block-scaled fp4 instruction (kind::mxf4, K = 64
+// per instruction) multiplies every 32-element block by a scale factor,
+// here 2^0 everywhere (ue8m0 0x7F), and accumulates in float32, where every
+// partial sum is an integer of magnitude <= d < 2^24, so D = Q S^T holds
+// b2sp exactly.  Delta = 2x - 2 b2sp for codes with x non-zeros each.
+// Packed fp4 moves half the bytes of an 8-bit operand per element and the
+// instruction does twice the e4m3 work per clock; the dense int8 kind does
+// not exist on this target.
 //
 // Kernel (persistent: one CTA per SM, or one CTA pair per two SMs, looping
 // over work items = (query tile, database slice)):
-//   warp 0      TMA producer: K-chunks of 128 bytes of the query tile (A,
-//               128 x 128 B) and of the database tile (B, 256 x 128 B, or its
-//               half for a CTA pair), SWIZZLE_128B, through a ring of
-//               mbarrier stages;
-//   warp 1      allocates 512 TMEM columns, issues tcgen05.mma
-//               (M = 128 or, for a pair, 256; N = 256; K = 32) from one thread
-//               into one of two accumulators (256 columns each), commits
-//               stage releases and accumulator-ready signals with
-//               tcgen05.commit (multicast to both CTAs of a pair);
+//   warp 0      TMA producer: K-chunks of 128 bytes (256 elements) of the
+//               query tile (A, 128 x 128 B) and of the database tile (B,
+//               240 x 128 B, or its half for a CTA pair), SWIZZLE_128B,
+//               through a ring of mbarrier stages;
+//   warp 1      allocates the 512 TMEM columns -- two accumulators of 240
+//               columns and the scale factors (32 columns of 2^0, written
+//               once by the epilogue warps) -- and issues tcgen05.mma
+//               (M = 128 or, for a pair, 256; N = 240; K = 64) from one
+//               thread into one of the accumulators, commits stage releases
+//               and accumulator-ready signals with tcgen05.commit
+//               (multicast to both CTAs of a pair);
 //   warp 6      threshold helper: recomputes each query's union bound (below)
 //               from the workspace histogram and publishes it in shared memory;
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator (thread = TMEM lane
@@ -57,9 +63,13 @@ namespace evp {
 namespace {
 
 constexpr int MMA_M = 128;   // query rows per CTA (= TMEM lanes)
-constexpr int MMA_N = 256;   // database rows per accumulator tile
-constexpr int MMA_K = 32;
-constexpr int KCHUNK = 128;
+constexpr int MMA_N = MMA_TILE_ROWS;  // database rows per accumulator tile (240)
+constexpr int KSTEP = 32;    // bytes of K per instruction (64 fp4 elements)
+constexpr int KCHUNK = 128;  // bytes of K per stage (256 elements)
+constexpr int EPI_GROUPS = (MMA_N + 31) / 32;  // 32-column TMEM loads per tile (the last: 16 columns)
+static_assert(EPI_GROUPS % 2 == 0, "the epilogue loads groups in pairs");
+static_assert(MMA_N % 16 == 0 && MMA_N > 224 && MMA_N <= 256, "N of the instruction, last group");
+constexpr uint32_t SF_COL = 2 * MMA_N;  // scale factors: A at column 480, B at 488 (<= 8 each)
 constexpr int HEAP_SLOTS = 128 * 128;  // heap capacity: active queries x k <= 128 x 128
 constexpr int NUM_THREADS = 224;  // TMA, MMA, 4 epilogue warps, threshold helper
 constexpr int EPI_WARPS = 4;
@@ -71,6 +81,7 @@ constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
 // A 32-column group can stage up to 32 keys per lane right after a flush.
 static_assert(STAGE_SLOTS >= 32, "staging must hold one full column group");
 constexpr uint32_t TMEM_COLS = 512;
+static_assert(SF_COL + 32 <= TMEM_COLS, "TMEM columns");
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
 constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
 constexpr int UBOUND_BYTES = MMA_M * 8;             // helper -> epilogue thresholds
@@ -90,10 +101,11 @@ struct MmaCfg {
     static constexpr int STAGES = CG == 2 ? 4 : 3;
     static constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES +
                                          STAGING_BYTES + UBOUND_BYTES + 256;
-    // Instruction descriptor: D = f32, A = B = e4m3 (format 0), both
-    // K-major, N = 256, M = 128 x CG.
-    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(MMA_N >> 3) << 17) |
-                                      ((uint32_t)((MMA_M * CG) >> 4) << 24);
+    // Instruction descriptor of the block-scaled kinds: A = B = e2m1
+    // (format 1 of kind::mxf4), both K-major, N = 240, scale factors ue8m0
+    // (bit 23), M = 128 x CG; scale-factor IDs 0.
+    static constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
+                                      (1u << 23) | ((uint32_t)((MMA_M * CG) >> 4) << 24);
 };
 static_assert(MmaCfg<1>::SMEM_BYTES <= 232448 && MmaCfg<2>::SMEM_BYTES <= 232448,
               "shared memory per CTA");
@@ -141,24 +153,39 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return r;
 }
 
+// D (+)= A B^T over one K step: e2m1 operands in shared memory, unit scale
+// factors in tensor memory (sfa, sfb).
 template <int CG>
-__device__ __forceinline__ void mma_f8(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t accumulate) {
+__device__ __forceinline__ void mma_f4(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t sfa, uint32_t sfb, uint32_t accumulate) {
     if constexpr (CG == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-            "l"(adesc), "l"(bdesc), "r"(MmaCfg<1>::IDESC), "r"(accumulate)
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X "
+            "[%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(MmaCfg<1>::IDESC), "r"(sfa), "r"(sfb), "r"(accumulate)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-            "l"(adesc), "l"(bdesc), "r"(MmaCfg<2>::IDESC), "r"(accumulate)
+            "setp.ne.b32 p, %6, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X "
+            "[%0], %1, %2, %3, [%4], [%5], p;\n\t}" ::"r"(dtmem),
+            "l"(adesc), "l"(bdesc), "r"(MmaCfg<2>::IDESC), "r"(sfa), "r"(sfb), "r"(accumulate)
             : "memory");
     }
+}
+
+// Write v to 32 consecutive columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, "
+        "%1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1, %1};" ::"r"(taddr),
+        "r"(v)
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // One arrival on `bar` once every MMA issued so far has completed: on this
@@ -407,6 +434,13 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if constexpr (CG == 2) cluster_sync_all();  // the peer's barriers are initialised
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // unit scale factors (ue8m0 2^0) in columns 480-511 of every lane, before any MMA
+    if (warp >= 2 && warp < 2 + EPI_WARPS)
+        tmem_fill32(tmem_base + ((uint32_t)((warp & 3) * 32) << 16) + SF_COL, 0x7F7F7F7Fu);
+    tc_fence_before();
+    __syncthreads();
+    if constexpr (CG == 2) cluster_sync_all();  // both CTAs' scale factors are written
+    tc_fence_after();
     // Raise the abort flag here and, for a pair, in the other CTA.
     auto raise_abort = [&]() {
         *(volatile int*)abort_flag = 1;
@@ -482,7 +516,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         if (lane == 0 && leader) {
             // ---------------- MMA issuer ----------------
             // CG = 2: the shared-memory descriptors name this CTA's stage;
-            // the instruction reads the same offsets in the peer CTA.
+            // the instruction reads the same offsets in the peer CTA (and
+            // the scale factors at the same TMEM columns).
+            const uint32_t sfa = tmem_base + SF_COL, sfb = tmem_base + SF_COL + 8u;
             int it = 0, tt = 0;
             bool ok = true;
             for (int item = worker; item < nitems && ok; item += nworkers) {
@@ -508,9 +544,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
                     const uint32_t sb = sa + A_STAGE_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < KCHUNK / MMA_K; ++kk) {
-                        mma_f8<CG>(dt, sw128_desc(sa + kk * MMA_K), sw128_desc(sb + kk * MMA_K),
-                                   (kc > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < KCHUNK / KSTEP; ++kk) {
+                        mma_f4<CG>(dt, sw128_desc(sa + kk * KSTEP), sw128_desc(sb + kk * KSTEP),
+                                   sfa, sfb, (kc > 0 || kk > 0) ? 1u : 0u);
                     }
                     mma_commit_all<CG>(&empty[s]);
                 }
@@ -618,8 +654,11 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                                        fmaxf(sm[6], sm[7]));
                 float thr = fmaxf(dtau, dglob);
                 if (!__any_sync(0xffffffffu, valid_q && mx > thr)) return;
-                // columns of this group inside the slice (the last tile is ragged)
-                const int64_t left = row_end - (tile_row + c * 32);
+                // columns of this group inside the tile (the last group has
+                // MMA_N - 224 = 16; the rest of its load is another
+                // accumulator's or the scale factors) and inside the slice
+                // (the last tile is ragged)
+                const int64_t left = min(row_end - (tile_row + c * 32), (int64_t)(MMA_N - 32 * c));
                 const int lim = !valid_q ? 0 : (left >= 32 ? 32 : (left > 0 ? (int)left : 0));
                 uint32_t my8 = 0;  // this lane's 4-column sub-groups with a candidate
 #pragma unroll
@@ -661,16 +700,16 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             tmem_ld32_async(tbase, va);
             tmem_wait_ld(va);
 #pragma unroll 1
-            for (int c = 0; c < MMA_N / 32; c += 2) {
+            for (int c = 0; c < EPI_GROUPS; c += 2) {
                 __syncwarp();
                 tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), vb);
                 group(va, c);
                 __syncwarp();
                 tmem_wait_ld(vb);
-                if (c + 2 < MMA_N / 32) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), va);
+                if (c + 2 < EPI_GROUPS) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), va);
                 group(vb, c + 1);
                 __syncwarp();
-                if (c + 2 < MMA_N / 32) tmem_wait_ld(va);
+                if (c + 2 < EPI_GROUPS) tmem_wait_ld(va);
             }
             tc_fence_before();
             __syncwarp();
@@ -818,35 +857,42 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     }
 }
 
-// Packed codes -> e4m3 rows [n][Kp] (Kp a multiple of 128; columns >= d are 0).
-// spread_cg > 0: row i goes to lane_of_query(i, spread_cg) instead of i.
-__global__ void unpack_fp8_kernel(const uint64_t* __restrict__ T, int64_t n, int W, int Kp,
-                                  int spread_cg, uint8_t* __restrict__ out) {
-    const int groups = Kp / 16;
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t row = idx / groups;
-    if (row >= n) return;
-    const int g = (int)(idx - row * groups);
-    const int j0 = g * 16, w = j0 >> 6, sh = j0 & 63;
-    uint32_t p = 0, q = 0;
-    if (w < W) {
-        p = (uint32_t)((T[row * 2 * W + w] >> sh) & 0xFFFFu);
-        q = (uint32_t)((T[row * 2 * W + W + w] >> sh) & 0xFFFFu);
-    }
+// 32 elements of a code (bits of the + and - planes) -> 16 bytes of e2m1,
+// element e in nibble e (+1 -> 0x2, -1 -> 0xA, 0 -> 0; a set + bit wins).
+__device__ __forceinline__ uint4 e2m1_pack32(uint32_t pp, uint32_t mm) {
     uint32_t o[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         uint32_t word = 0;
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const int e = i * 4 + b;
-            const uint32_t byte = ((p >> e) & 1u) ? 0x38u : (((q >> e) & 1u) ? 0xB8u : 0u);
-            word |= byte << (8 * b);
+        for (int b = 0; b < 8; ++b) {
+            const int e = i * 8 + b;
+            const uint32_t nib = ((pp >> e) & 1u) ? 0x2u : (((mm >> e) & 1u) ? 0xAu : 0u);
+            word |= nib << (4 * b);
         }
         o[i] = word;
     }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// Packed codes -> e2m1 rows [n][Kp bytes] (Kp a multiple of 128; elements
+// >= d are 0).  spread_cg > 0: row i goes to lane_of_query(i, spread_cg)
+// instead of i.
+__global__ void unpack_fp4_kernel(const uint64_t* __restrict__ T, int64_t n, int W, int Kp,
+                                  int spread_cg, uint8_t* __restrict__ out) {
+    const int groups = Kp / 16;  // 16 bytes = 32 elements per thread
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t row = idx / groups;
+    if (row >= n) return;
+    const int g = (int)(idx - row * groups);
+    const int j0 = g * 32, w = j0 >> 6, sh = j0 & 63;
+    uint32_t p = 0, q = 0;
+    if (w < W) {
+        p = (uint32_t)(T[row * 2 * W + w] >> sh);
+        q = (uint32_t)(T[row * 2 * W + W + w] >> sh);
+    }
     const int64_t orow = spread_cg > 0 ? lane_of_query(row, spread_cg) : row;
-    reinterpret_cast<uint4*>(out + orow * (int64_t)Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
+    reinterpret_cast<uint4*>(out + orow * (int64_t)Kp)[g] = e2m1_pack32(p, q);
 }
 
 __global__ void init_tau_n_kernel(uint64_t* tau, int n, uint32_t* hist, int64_t hist_words,
@@ -864,7 +910,9 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 }  // namespace
 
-int mma_kp(int d) { return (d + KCHUNK - 1) / KCHUNK * KCHUNK; }
+// Bytes per row of the e2m1 operand copies: d elements, two per byte, padded
+// to whole 128-byte K chunks.
+int mma_kp(int d) { return (d + 2 * KCHUNK - 1) / (2 * KCHUNK) * KCHUNK; }
 
 // Queries served per 128-row tile: all 128 while their heaps fit
 // (k <= 128); for larger k fewer queries share the tile (the other rows of
@@ -956,13 +1004,13 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
     return p;
 }
 
-cudaError_t launch_unpack_fp8(const uint64_t* T, int64_t n, int d, uint8_t* out,
+cudaError_t launch_unpack_fp4(const uint64_t* T, int64_t n, int d, uint8_t* out,
                               cudaStream_t stream, int spread_cg) {
     if (n <= 0) return cudaSuccess;
     const int W = (d + 63) / 64, Kp = mma_kp(d);
     const int64_t threads = n * (Kp / 16);
-    TimedLaunch timer("unpack_fp8", stream);
-    unpack_fp8_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(T, n, W, Kp,
+    TimedLaunch timer("unpack_fp4", stream);
+    unpack_fp4_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(T, n, W, Kp,
                                                                                spread_cg, out);
     return cudaGetLastError();
 }
@@ -987,9 +1035,9 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     if ((reinterpret_cast<uintptr_t>(B8) & 255) != 0) return EVP_ERR_INVALID;
 
     if (p.spread && cudaMemsetAsync(A8, 0, p.a_bytes, stream) != cudaSuccess) return EVP_ERR_CUDA;
-    if (launch_unpack_fp8(Q, nq, d, A8, stream, p.spread ? p.cg : 0) != cudaSuccess)
+    if (launch_unpack_fp4(Q, nq, d, A8, stream, p.spread ? p.cg : 0) != cudaSuccess)
         return EVP_ERR_CUDA;
-    if (!S8 && launch_unpack_fp8(S, ns, d, B8, stream) != cudaSuccess) return EVP_ERR_CUDA;
+    if (!S8 && launch_unpack_fp4(S, ns, d, B8, stream) != cudaSuccess) return EVP_ERR_CUDA;
     {
         TimedLaunch timer("scan_init", stream);
         const int64_t hw = nq * (int64_t)hist_bins;
@@ -1073,9 +1121,9 @@ namespace {
 
 struct PrepBatch {
     const uint64_t* Q;    // packed query codes [nq][2W]
-    int64_t nq, rows;     // queries, and rows of the e4m3 query operand written
+    int64_t nq, rows;     // queries, and rows of the e2m1 query operand written
     int W, Kp, spread_cg;
-    uint8_t* A8;          // [rows][Kp] e4m3 query operand
+    uint8_t* A8;          // [rows][Kp bytes] e2m1 query operand
     uint64_t* tau;        // [nq]
     uint32_t* minhalf;    // [nq]
     uint32_t* hist;       // [hist_words]
@@ -1095,22 +1143,13 @@ __global__ void multi_prep_kernel(const PrepBatch* __restrict__ tab) {
         const int64_t R = idx / groups;
         const int g = (int)(idx - R * groups);
         const int64_t q = p.spread_cg > 0 ? query_of_lane((int)(R & 127), (int)(R >> 7), p.spread_cg) : R;
-        uint32_t o[4] = {0u, 0u, 0u, 0u};
-        const int j0 = g * 16, w = j0 >> 6, sh = j0 & 63;
+        const int j0 = g * 32, w = j0 >> 6, sh = j0 & 63;
+        uint32_t pp = 0, mm = 0;
         if (q < p.nq && w < p.W) {
-            const uint32_t pp = (uint32_t)((p.Q[q * 2 * p.W + w] >> sh) & 0xFFFFu);
-            const uint32_t mm = (uint32_t)((p.Q[q * 2 * p.W + p.W + w] >> sh) & 0xFFFFu);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int e = i * 4 + b;
-                    const uint32_t byte = ((pp >> e) & 1u) ? 0x38u : (((mm >> e) & 1u) ? 0xB8u : 0u);
-                    o[i] |= byte << (8 * b);
-                }
-            }
+            pp = (uint32_t)(p.Q[q * 2 * p.W + w] >> sh);
+            mm = (uint32_t)(p.Q[q * 2 * p.W + p.W + w] >> sh);
         }
-        reinterpret_cast<uint4*>(p.A8 + R * (int64_t)p.Kp)[g] = make_uint4(o[0], o[1], o[2], o[3]);
+        reinterpret_cast<uint4*>(p.A8 + R * (int64_t)p.Kp)[g] = e2m1_pack32(pp, mm);
     }
     for (int64_t i = i0; i < p.nq; i += stride) {
         p.tau[i] = KEY_NONE;
@@ -1275,7 +1314,7 @@ int32_t mma_multi_create(const MmaBatchSpec* specs, int nb, MmaMultiPlan** out) 
 int32_t mma_multi_run(MmaMultiPlan* P, int32_t* status, cudaStream_t stream) {
     if (!P) return EVP_ERR_INVALID;
     {
-        TimedLaunch timer("unpack_fp8", stream);
+        TimedLaunch timer("unpack_fp4", stream);
         const int64_t bx = std::min<int64_t>((P->max_rows_groups + 255) / 256, (int64_t)num_sms() * 4);
         multi_prep_kernel<<<dim3((unsigned)std::max<int64_t>(1, bx), (unsigned)P->nb), 256, 0,
                             stream>>>(P->prep);

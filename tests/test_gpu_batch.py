@@ -113,7 +113,7 @@ def test_fused_plan_matches_separate_and_oracle(evp_lib, dev, dbs, graph, tune):
     sep = evp_lib.BatchPlan(spec, graph=False, tune=tune, fused=False, stream=stream)
     assert sep.fused == 0
     if not tune:
-        assert fused.fused == 6          # the batches the automatic rule gives the e4m3 scan
+        assert fused.fused == 6          # the batches the automatic rule gives the fp4 scan
     st = evp_lib.new_status(dev)
     with torch.cuda.stream(stream):
         fused.run(status=st, stream=stream)

@@ -6,7 +6,7 @@
 * 10,000,000 x 768, x = 512 (the benchmark's database): every code of the
   database compared with the oracle's, and the exhaustive kNN (Sec. 5.3)
   of the oracle over all 10M rows compared id by id and Delta by Delta with
-  each scan path -- the popcount scan (40 queries, three passes), the e4m3
+  each scan path -- the popcount scan (40 queries, three passes), the fp4
   tensor-core scan in the benchmark's launch configuration (1,024 queries,
   shortlist 100, then the rerank to 10) and the packed tensor-core scan
   (16 and 64 queries) -- on queries spread over passes, query tiles and
@@ -112,7 +112,7 @@ def test_10m_768_popcount_scan_exhaustive(evp_lib, dev, db_10m_768):
 
 def test_10m_768_bench_launch_exhaustive(evp_lib, dev, db_10m_768):
     """The benchmark's step: 1,024 float queries through the resident
-    database's search (encode -> e4m3 tensor-core scan for the shortlist of
+    database's search (encode -> fp4 tensor-core scan for the shortlist of
     100 -> rerank to 10), plus the plain kNN of the same launch."""
     D = db_10m_768
     n_sl, k = 100, 10
@@ -120,7 +120,7 @@ def test_10m_768_bench_launch_exhaustive(evp_lib, dev, db_10m_768):
     db = evp_lib.Database(D["Ts"], D["U"], D["d"], D["x"])
     Tq = evp_lib.encode(D["Q"], D["x"], status=st)
     sl, sd = db.knn(Tq, n_sl, status=st, path=evp_lib.PATH_MMA)
-    sl_a, sd_a = db.knn(Tq, n_sl, status=st)       # the automatic choice (e4m3 here)
+    sl_a, sd_a = db.knn(Tq, n_sl, status=st)       # the automatic choice (fp4 here)
     rid, rsc = db.search(D["Q"], n_sl, k, status=st)
     torch.cuda.synchronize()
     assert int(st.item()) == 0

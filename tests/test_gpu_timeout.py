@@ -22,7 +22,7 @@ def _case(evp, dev, ns, nq, d, x, stream):
 
 
 @pytest.mark.parametrize("path,nq,fills", [
-    (2, 300, 0),     # e4m3 tensor-core scan (CTA pairs): first CTA issues nothing
+    (2, 300, 0),     # fp4 tensor-core scan (CTA pairs): first CTA issues nothing
     (2, 300, 7),     # ... stalls mid-tile, its pair peer has issued more
     (3, 16, 0),      # packed tensor-core scan
     (3, 40, 5),
