@@ -170,7 +170,8 @@ size_t evp::knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool co
     if ((path == EVP_PATH_MMA || path == EVP_PATH_AUTO) && k <= MMA_K_MAX && nq >= nq0) {
         const int64_t qa = mma_active_queries(k);
         for (int64_t t = (nq0 + qa - 1) / qa; t <= (nq + qa - 1) / qa; ++t)
-            best = std::max(best, plan_mma_scan(std::min(nq, t * qa), ns, d, k, convert_db).ws_bytes);
+            best = std::max(best,
+                            plan_mma_scan(std::min(nq, t * qa), ns, d, k, convert_db, 0, true).ws_bytes);
     }
     return best;
 }

@@ -267,15 +267,17 @@ int32_t run_popc_knn(const uint64_t* Q, int64_t nq, const uint64_t* S, int64_t n
                      int x, int k, int64_t* ids, int32_t* dist, void* ws, size_t ws_bytes,
                      int32_t* status, cudaStream_t stream);
 
-// Per-query merge of per-(query, slice) sorted key lists ([nq][nslices][2][k]
-// with meta [nq][nslices] = (length, buffer)) into the k best.  Histogram
+// Per-query merge of per-(query, slice) sorted key lists ([nq][nslices][2][kl]
+// with meta [nq][nslices] = (length, buffer)) into the k best; kl = list
+// capacity (0: k; a scan with capped lists passes kl < k).  Histogram
 // bins count Delta/2 (bin_shift < 0) or (key >> 32) >> bin_shift; the
 // output distance is key >> 32, or dist_bias - (key >> 32) when dist_bias
 // is not 0 (the score of the int8-query scan).
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
                            const uint32_t* hist, const uint32_t* minhalf, int hist_bins,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
-                           cudaStream_t stream, int bin_shift = -1, int dist_bias = 0);
+                           cudaStream_t stream, int bin_shift = -1, int dist_bias = 0,
+                           int kl = 0);
 
 // One batch of a multi-batch final merge: queries q0 .. q0 + nq - 1 of the
 // launch are queries 0 .. nq - 1 of this batch (Delta keys).
@@ -285,7 +287,7 @@ struct FmBatch {
     const uint64_t* tau;
     const uint32_t* hist;
     const uint32_t* minhalf;
-    int hist_bins, nslices, k, stage;
+    int hist_bins, nslices, k, kl, stage;  // kl: list capacity (<= k)
     int64_t q0;
     int64_t* ids;
     int32_t* dist;
@@ -308,6 +310,7 @@ int32_t run_merge_topk(const int64_t* ids, const int32_t* dist, int64_t nq, int 
 
 struct MmaPlan {
     int kp;                 // bytes per row of the e2m1 operands (a multiple of 128)
+    int kl;                 // keys kept per (query, slice): k, or 128 with capped lists
     int qa;                 // active queries per 128-row tile
     int qtiles;             // query tiles (of qa queries)
     int nslices;            // database slices per query tile
@@ -338,8 +341,12 @@ size_t knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert
 int mma_active_queries(int k);
 // tiles_per_item > 0: slices of about that many 240-row database tiles (the
 // tile shape of the fused multi-batch scan) instead of whole waves.
+// allow_cap: for k > 128, keep 128 keys per (query, slice) -- every query
+// lane of a tile active -- when the slices are many enough that a slice
+// rarely holds more than 64 of a query's k nearest (nslices x 64 >= k); a
+// repair pass then makes the result exact (run_mma_knn).
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
-                      int tiles_per_item = 0);
+                      int tiles_per_item = 0, bool allow_cap = false);
 
 // Fused multi-batch tensor-core scan (the batched form): several kNN
 // batches, each against a resident e2m1 database copy, scanned by one

@@ -115,7 +115,8 @@ struct MmaArgs {
     int64_t ns;
     int kchunks;
     int x;
-    int k;
+    int k;                 // keys kept per (query, slice): heap and list capacity
+    int kunion;            // the query's k: the union bound is its kunion-th smallest counted key
     int64_t rows_per_slice;
     int qtiles, nslices;   // work items = qtiles * nslices
     int qa;                // active queries per 128-row tile (k <= HEAP_SLOTS / qa)
@@ -797,7 +798,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 #pragma unroll
                     for (int u = 0; u < 16; ++u) {
                         cum += c16[u];
-                        if (!found && cum >= (uint32_t)a.k && h0 + u < best[j]) {
+                        if (!found && cum >= (uint32_t)a.kunion && h0 + u < best[j]) {
                             best[j] = h0 + u;
                             found = true;
                         }
@@ -895,6 +896,119 @@ __global__ void unpack_fp4_kernel(const uint64_t* __restrict__ T, int64_t n, int
     reinterpret_cast<uint4*>(out + orow * (int64_t)Kp)[g] = e2m1_pack32(p, q);
 }
 
+// ---- exactness of a scan with capped lists ------------------------------
+// With k > 128 the scan may keep only kl = 128 keys per (query, slice) list
+// (every query lane of a tile then stays active).  The merged result is the
+// k best of the lists; it is exact unless some slice holds more than kl of
+// the keys below the result's k-th key T.  A slice can do so only if its
+// list is full and the list's last key lies below T: those (query, slice)
+// pairs are rescanned here, one CTA per query, by popcount on the packed
+// codes with the scan's own Delta (2 clamp(x - b2sp, 0, 2x), so the keys
+// equal the scan's), keeping the keys between the list's last key and the
+// current k-th key; the result is re-selected from its k keys and those
+// (block bitonic sort), T tightening as it goes.  Rows are randomly ordered
+// with respect to a query, so with the slice counts the capped plan
+// requires (at least 2k/kl slices) the rescan is rarely needed; it keeps
+// the result exact when it is.
+constexpr int RP_THREADS = 256;
+constexpr int RP_BUF = 2048;           // keys appended between two selections
+constexpr int RP_SORT = 4096;          // >= EVP_MMA_MAX_K + RP_BUF, a power of two
+static_assert(MMA_K_MAX + RP_BUF <= RP_SORT, "repair sort buffer");
+constexpr int RP_W_MAX = 16;
+
+__device__ void rp_block_sort(uint64_t* b, int n) {
+    for (int kk = 2; kk <= n; kk <<= 1)
+        for (int j = kk >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += RP_THREADS) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const uint64_t a0 = b[i], a1 = b[ixj];
+                    if ((a0 > a1) == ((i & kk) == 0)) {
+                        b[i] = a1;
+                        b[ixj] = a0;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__global__ void __launch_bounds__(RP_THREADS) repair_capped_kernel(
+    const uint64_t* __restrict__ Q, const uint64_t* __restrict__ S, int64_t ns, int W, int x,
+    const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta, int nslices, int kl,
+    int64_t rows_per_slice, int k, int64_t* __restrict__ ids, int32_t* __restrict__ dist,
+    uint32_t* __restrict__ repaired) {
+    extern __shared__ __align__(16) uint64_t rp_buf[];  // [RP_SORT]
+    __shared__ uint64_t qw[2 * RP_W_MAX];
+    __shared__ int cnt, any;
+    const int64_t q = blockIdx.x;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 2 * W; i += RP_THREADS) qw[i] = Q[q * 2 * W + i];
+    // the merged result as keys; T = its k-th key
+    for (int i = tid; i < k; i += RP_THREADS) {
+        const int64_t id = ids[q * k + i];
+        rp_buf[i] = id < 0 ? KEY_NONE : ((uint64_t)(uint32_t)dist[q * k + i] << 32) | (uint64_t)id;
+    }
+    if (tid == 0) any = 0;
+    __syncthreads();
+    uint64_t T = rp_buf[k - 1];
+    auto last_of = [&](int s, int* len) {
+        const int64_t e = (q * nslices + s) * 2;
+        *len = min(max(meta[e], 0), kl);
+        return *len > 0 ? lists[(e + (meta[e + 1] & 1)) * kl + *len - 1] : 0ull;
+    };
+    // selection of the k best of rp_buf[0, k + cnt)
+    auto select = [&]() {
+        const int n = k + cnt;
+        int P = 2;
+        while (P < n) P <<= 1;
+        for (int i = n + tid; i < P; i += RP_THREADS) rp_buf[i] = KEY_NONE;
+        __syncthreads();
+        rp_block_sort(rp_buf, P);
+        T = rp_buf[k - 1];
+        __syncthreads();
+        if (tid == 0) cnt = 0;
+        __syncthreads();
+    };
+    for (int s = 0; s < nslices; ++s) {
+        int len;
+        const uint64_t lo = last_of(s, &len);
+        if (len < kl || (T != KEY_NONE && lo >= T)) continue;  // the list holds all its keys below T
+        if (tid == 0) {
+            cnt = 0;
+            any = 1;
+        }
+        __syncthreads();
+        const int64_t r0 = (int64_t)s * rows_per_slice;
+        const int64_t r1 = min(r0 + rows_per_slice, ns);
+        for (int64_t b0 = r0; b0 < r1; b0 += RP_THREADS) {
+            const int64_t row = b0 + tid;
+            if (row < r1) {
+                const uint64_t* sr = S + row * 2 * W;
+                int dot = 0;
+                for (int w = 0; w < W; ++w) {
+                    const uint64_t sp = sr[w], sm = sr[W + w];
+                    dot += __popcll(qw[w] & sp) + __popcll(qw[W + w] & sm) -
+                           __popcll(qw[w] & sm) - __popcll(qw[W + w] & sp);
+                }
+                const uint32_t half = (uint32_t)min(max(x - dot, 0), 2 * x);
+                const uint64_t key = ((uint64_t)(2u * half) << 32) | (uint64_t)row;
+                if (key > lo && key < T) rp_buf[k + atomicAdd(&cnt, 1)] = key;
+            }
+            __syncthreads();
+            if (cnt > RP_BUF - RP_THREADS) select();  // the next round adds <= RP_THREADS
+        }
+        if (cnt > 0) select();
+    }
+    if (!any) return;
+    for (int j = tid; j < k; j += RP_THREADS) {
+        const uint64_t key = rp_buf[j];
+        ids[q * k + j] = key == KEY_NONE ? -1 : (int64_t)(key & 0xffffffffull);
+        dist[q * k + j] = key == KEY_NONE ? -1 : (int32_t)(key >> 32);
+    }
+    if (tid == 0 && repaired) atomicAdd(repaired, 1u);
+}
+
 __global__ void init_tau_n_kernel(uint64_t* tau, int n, uint32_t* hist, int64_t hist_words,
                                   uint32_t* minhalf) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -960,48 +1074,59 @@ int mma_pair_workers() {
 }
 
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
-                      int tiles_per_item) {
-    MmaPlan p{};
-    p.kp = mma_kp(d);
-    p.qa = mma_active_queries(k);
-    p.qtiles = (int)((nq + p.qa - 1) / p.qa);
-    const int pairs = mma_pair_workers();
-    p.cg = pairs > 0 ? 2 : 1;
-    p.workers = pairs > 0 ? pairs : num_sms();
-    // a single tile's worth of queries is spread over every epilogue warp
-    // (and both CTAs of a pair), so that no warp carries all the candidates
-    p.spread = p.qa == MMA_M && nq <= MMA_M;
-    if (p.spread) p.qtiles = p.cg;
-    const int units = (p.qtiles + p.cg - 1) / p.cg;
-    const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
-    const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
-    // units * slices a multiple of the resident workers (whole waves of the
-    // persistent grid), at least min_slices, at most one slice per tile
-    const int64_t sms = p.workers;
-    int64_t g = sms, b = std::max(1, units);
-    while (b) {
-        const int64_t r = g % b;
-        g = b;
-        b = r;
+                      int tiles_per_item, bool allow_cap) {
+    // kl keys per (query, slice) list and heap
+    auto build = [&](int kl) {
+        MmaPlan p{};
+        p.kp = mma_kp(d);
+        p.kl = kl;
+        p.qa = mma_active_queries(kl);
+        p.qtiles = (int)((nq + p.qa - 1) / p.qa);
+        const int pairs = mma_pair_workers();
+        p.cg = pairs > 0 ? 2 : 1;
+        p.workers = pairs > 0 ? pairs : num_sms();
+        // a single tile's worth of queries is spread over every epilogue warp
+        // (and both CTAs of a pair), so that no warp carries all the candidates
+        p.spread = p.qa == MMA_M && nq <= MMA_M;
+        if (p.spread) p.qtiles = p.cg;
+        const int units = (p.qtiles + p.cg - 1) / p.cg;
+        const int64_t ntiles = (ns + MMA_N - 1) / MMA_N;
+        const int64_t min_slices = (ns + MAX_SLICE_ROWS - 1) / MAX_SLICE_ROWS;
+        // units * slices a multiple of the resident workers (whole waves of the
+        // persistent grid), at least min_slices, at most one slice per tile
+        const int64_t sms = p.workers;
+        int64_t g = sms, b = std::max(1, units);
+        while (b) {
+            const int64_t r = g % b;
+            g = b;
+            b = r;
+        }
+        const int64_t step = sms / g;
+        int64_t slices = step;
+        while (slices < min_slices) slices += step;
+        // a given tile shape (the fused multi-batch scan): slices of about
+        // tiles_per_item database tiles each
+        if (tiles_per_item > 0)
+            slices = std::max(min_slices, (ntiles + tiles_per_item - 1) / tiles_per_item);
+        slices = std::min(slices, std::max<int64_t>(1, ntiles));
+        const int64_t tiles_per_slice = (ntiles + slices - 1) / slices;
+        p.rows_per_slice = tiles_per_slice * MMA_N;
+        p.nslices = (int)((ns + p.rows_per_slice - 1) / p.rows_per_slice);
+        p.a_bytes = align256((size_t)p.qtiles * MMA_M * p.kp);
+        p.b_bytes = convert_db ? align256((size_t)ns * p.kp) : 0;
+        p.list_bytes = align256((size_t)nq * p.nslices * 2 * kl * 8);
+        p.meta_bytes = align256((size_t)nq * p.nslices * 2 * 4);
+        p.tau_bytes = align256((size_t)nq * 8);
+        p.hist_bytes = align256((size_t)nq * (2 * d + 1) * 4) + align256((size_t)nq * 4);
+        p.ws_bytes = p.a_bytes + p.b_bytes + p.list_bytes + p.meta_bytes + p.tau_bytes +
+                     p.hist_bytes;
+        return p;
+    };
+    if (allow_cap && k > MMA_M && tiles_per_item == 0) {
+        const MmaPlan c = build(MMA_M);
+        if ((int64_t)c.nslices * (MMA_M / 2) >= k) return c;
     }
-    const int64_t step = sms / g;
-    int64_t slices = step;
-    while (slices < min_slices) slices += step;
-    // a given tile shape (the fused multi-batch scan): slices of about
-    // tiles_per_item database tiles each
-    if (tiles_per_item > 0) slices = std::max(min_slices, (ntiles + tiles_per_item - 1) / tiles_per_item);
-    slices = std::min(slices, std::max<int64_t>(1, ntiles));
-    const int64_t tiles_per_slice = (ntiles + slices - 1) / slices;
-    p.rows_per_slice = tiles_per_slice * MMA_N;
-    p.nslices = (int)((ns + p.rows_per_slice - 1) / p.rows_per_slice);
-    p.a_bytes = align256((size_t)p.qtiles * MMA_M * p.kp);
-    p.b_bytes = convert_db ? align256((size_t)ns * p.kp) : 0;
-    p.list_bytes = align256((size_t)nq * p.nslices * 2 * k * 8);
-    p.meta_bytes = align256((size_t)nq * p.nslices * 2 * 4);
-    p.tau_bytes = align256((size_t)nq * 8);
-    p.hist_bytes = align256((size_t)nq * (2 * d + 1) * 4) + align256((size_t)nq * 4);
-    p.ws_bytes = p.a_bytes + p.b_bytes + p.list_bytes + p.meta_bytes + p.tau_bytes + p.hist_bytes;
-    return p;
+    return build(k);
 }
 
 cudaError_t launch_unpack_fp4(const uint64_t* T, int64_t n, int d, uint8_t* out,
@@ -1019,7 +1144,7 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
                     int64_t ns, int d, int x, int k, int64_t* ids, int32_t* dist, void* ws,
                     size_t ws_bytes, int32_t* status, cudaStream_t stream) {
     if (k > MMA_K_MAX) return EVP_ERR_UNSUPPORTED;
-    const MmaPlan p = plan_mma_scan(nq, ns, d, k, S8 == nullptr);
+    const MmaPlan p = plan_mma_scan(nq, ns, d, k, S8 == nullptr, 0, S != nullptr);
     if (ws_bytes < p.ws_bytes) return EVP_ERR_NO_MEMORY;
     uint8_t* w = static_cast<uint8_t*>(ws);
     uint8_t* A8 = w;
@@ -1069,7 +1194,8 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.ns = ns;
     args.kchunks = p.kp / KCHUNK;
     args.x = x;
-    args.k = k;
+    args.k = p.kl;
+    args.kunion = k;
     args.rows_per_slice = p.rows_per_slice;
     args.qtiles = p.qtiles;
     args.qa = p.qa;
@@ -1111,8 +1237,16 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
             return EVP_ERR_CUDA;
     }
     if (cudaGetLastError() != cudaSuccess) return EVP_ERR_CUDA;
-    return launch_final_merge(lists, meta, tau, hist, minhalf, hist_bins, nq, p.nslices, k, ids,
-                              dist, stream);
+    const int32_t rc = launch_final_merge(lists, meta, tau, hist, minhalf, hist_bins, nq,
+                                          p.nslices, k, ids, dist, stream, -1, 0, p.kl);
+    if (rc != EVP_OK || p.kl >= k) return rc;
+    // capped lists: the exactness check and, where a slice may have left out
+    // keys, its rescan
+    TimedLaunch timer("scan_repair", stream);
+    repair_capped_kernel<<<(unsigned)nq, RP_THREADS, RP_SORT * 8, stream>>>(
+        Q, S, ns, (d + 63) / 64, x, lists, meta, p.nslices, p.kl, p.rows_per_slice, k, ids, dist,
+        nullptr);
+    return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
 
 
@@ -1255,6 +1389,7 @@ int32_t mma_multi_create(const MmaBatchSpec* specs, int nb, MmaMultiPlan** out) 
         A.kchunks = p.kp / KCHUNK;
         A.x = B.x;
         A.k = B.k;
+        A.kunion = B.k;
         A.rows_per_slice = p.rows_per_slice;
         A.qtiles = p.qtiles;
         A.qa = p.qa;
@@ -1275,7 +1410,7 @@ int32_t mma_multi_create(const MmaBatchSpec* specs, int nb, MmaMultiPlan** out) 
         int stage = 0;
         fm_smem = std::max(fm_smem, final_merge_smem(p.nslices, B.k, &stage));
         fm[b] = FmBatch{L.lists, L.meta, L.tau, L.hist, L.minhalf, A.hist_bins, p.nslices, B.k,
-                        stage, q0, B.ids, B.dist};
+                        B.k, stage, q0, B.ids, B.dist};
         q0 += B.nq;
         P->max_rows_groups = std::max<int>(P->max_rows_groups, (int)std::min<int64_t>(
                                                arows * (p.kp / 16), 1 << 30));

@@ -417,9 +417,10 @@ __device__ __forceinline__ int upper_bound_u64(const uint64_t* a, int n, uint64_
 __device__ __forceinline__ void final_merge_query(
     const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
     const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
-    const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k, int key_bits,
+    const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k, int kl, int key_bits,
     int stage_lists, int bin_shift, int dist_bias, int64_t* __restrict__ ids,
     int32_t* __restrict__ dist, const int64_t q, uint8_t* smem) {
+    // lists hold up to kl keys each (kl <= k: a scan with capped lists)
     __shared__ int red[FM_THREADS / 32];
     __shared__ int total_s;
     uint64_t* out = reinterpret_cast<uint64_t*>(smem);           // sort buffer
@@ -433,12 +434,12 @@ __device__ __forceinline__ void final_merge_query(
     // scan that gave up (EVP_ERR_TIMEOUT) some of them were never written,
     // and the merge must still stay inside the workspace.
     for (int s = tid; s < nslices; s += FM_THREADS)
-        lens[s] = min(max(meta[(qbase + s) * 2], 0), k);
+        lens[s] = min(max(meta[(qbase + s) * 2], 0), kl);
     __syncthreads();
     bool staged_now = false;
     auto list_ptr = [&](int s) -> const uint64_t* {
-        return staged_now ? staged + (int64_t)s * k
-                          : lists + ((qbase + s) * 2 + (meta[(qbase + s) * 2 + 1] & 1)) * k;
+        return staged_now ? staged + (int64_t)s * kl
+                          : lists + ((qbase + s) * 2 + (meta[(qbase + s) * 2 + 1] & 1)) * kl;
     };
     auto count_le = [&](uint64_t v) -> int {
         int c = 0;
@@ -497,9 +498,9 @@ __device__ __forceinline__ void final_merge_query(
     int m = T != KEY_NONE ? count_le(T) : FM_GATHER + 1;
     if (m < k || m > FM_GATHER) {
         if (stage_lists) {
-            for (int64_t e = tid; e < (int64_t)nslices * k; e += FM_THREADS) {
-                const int s = (int)(e / k), i = (int)(e - (int64_t)s * k);
-                if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + (meta[(qbase + s) * 2 + 1] & 1)) * k + i];
+            for (int64_t e = tid; e < (int64_t)nslices * kl; e += FM_THREADS) {
+                const int s = (int)(e / kl), i = (int)(e - (int64_t)s * kl);
+                if (i < lens[s]) staged[e] = lists[((qbase + s) * 2 + (meta[(qbase + s) * 2 + 1] & 1)) * kl + i];
             }
             __syncthreads();
             staged_now = true;
@@ -566,10 +567,10 @@ __global__ void __launch_bounds__(FM_THREADS)
 final_merge_kernel(const uint64_t* __restrict__ lists, const int32_t* __restrict__ meta,
                    const uint64_t* __restrict__ tau, const uint32_t* __restrict__ hist,
                    const uint32_t* __restrict__ minhalf, int hist_bins, int nslices, int k,
-                   int key_bits, int stage_lists, int bin_shift, int dist_bias,
+                   int kl, int key_bits, int stage_lists, int bin_shift, int dist_bias,
                    int64_t* __restrict__ ids, int32_t* __restrict__ dist) {
     extern __shared__ __align__(1024) uint8_t smem[];
-    final_merge_query(lists, meta, tau, hist, minhalf, hist_bins, nslices, k, key_bits,
+    final_merge_query(lists, meta, tau, hist, minhalf, hist_bins, nslices, k, kl, key_bits,
                       stage_lists, bin_shift, dist_bias, ids, dist, (int64_t)blockIdx.x, smem);
 }
 
@@ -587,7 +588,7 @@ final_merge_multi_kernel(const FmBatch* __restrict__ tab, int nb, int key_bits) 
     }
     const FmBatch& b = tab[lo];
     final_merge_query(b.lists, b.meta, b.tau, b.hist, b.minhalf, b.hist_bins, b.nslices, b.k,
-                      key_bits, b.stage, -1, 0, b.ids, b.dist, i - b.q0, smem);
+                      b.kl, key_bits, b.stage, -1, 0, b.ids, b.dist, i - b.q0, smem);
 }
 
 int choose_stages(int W, int qb) {
@@ -676,10 +677,11 @@ int32_t launch_final_merge_multi(const FmBatch* tab, int nb, int64_t total_q, si
 int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uint64_t* tau,
                            const uint32_t* hist, const uint32_t* minhalf, int hist_bins,
                            int64_t nq, int nslices, int k, int64_t* ids, int32_t* dist,
-                           cudaStream_t stream, int bin_shift, int dist_bias) {
+                           cudaStream_t stream, int bin_shift, int dist_bias, int kl) {
     if (nq <= 0) return EVP_OK;
     if (nslices > FM_MAX_SLICES) return EVP_ERR_UNSUPPORTED;
-    const size_t list_bytes = (size_t)nslices * k * 8;
+    if (kl <= 0 || kl > k) kl = k;
+    const size_t list_bytes = (size_t)nslices * kl * 8;
     const int stage = list_bytes <= (size_t)FM_STAGE_BYTES ? 1 : 0;
     const size_t smem = FM_OUT_BYTES + 2 * FM_MAX_SLICES * 4 + (stage ? list_bytes : 0);
     if (cudaFuncSetAttribute(final_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -690,7 +692,7 @@ int32_t launch_final_merge(const uint64_t* lists, const int32_t* meta, const uin
     const int key_bits = 32 + (bin_shift < 0 ? 13 : 18);
     TimedLaunch timer("final_merge", stream);
     final_merge_kernel<<<(unsigned)nq, FM_THREADS, smem, stream>>>(
-        lists, meta, tau, hist, minhalf, hist_bins, nslices, k, key_bits, stage, bin_shift,
+        lists, meta, tau, hist, minhalf, hist_bins, nslices, k, kl, key_bits, stage, bin_shift,
         dist_bias, ids, dist);
     return cudaGetLastError() == cudaSuccess ? EVP_OK : EVP_ERR_CUDA;
 }
