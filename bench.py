@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the batched-form and served-form measurements")
     ap.add_argument("--serve-seconds", type=float, default=3.0)
-    ap.add_argument("--serve-rates", default="50,100,150,200,300,400",
+    ap.add_argument("--serve-rates", default="100,200,400,800,1200,1600",
                     help="Poisson request rates (requests/s) of the served-form sweep")
     ap.add_argument("--recall-sweep", action="store_true",
                     help="instead of the benchmark: recall of the ternary scan against exact "
