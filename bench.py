@@ -142,18 +142,22 @@ KERNEL_SOURCES = {
                         "paper_2506_00528_gb300/csrc/evp_internal.cuh"],
 }
 MEASURED_TRAFFIC = {
-    # profiles/scan_mma_10Mx768_b1024_launches.md (DRAM capture of the same command)
+    # DRAM bytes of one launch at the 10M-row workload, from a capture of
+    # the same command on 1,000,000 rows (the recipe's size rule): reads
+    # scaled by the rows (the database stream), writes (per-query lists and
+    # histograms, independent of the rows) as captured.
+    # profiles/scan_mma_10Mx768_b1024_launches.md
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 7_683_557_888 + 4_296_192,
-        "sources_sha256": "35070e6b6dd2870f20da59cb6e36bafcf1c7e57217298adf2d4e973e0224849d"},
-    # profiles/scan_popc_1Mx768_b1_ncu.md (DRAM capture of the 10M, one-query command)
+        "bytes": 386_433_280 * 10 + 3_969_280,
+        "sources_sha256": "1f5e24cb456b30bd7cf5461230a2c284c8d4bdb8774ade8d495e1565718ba0b6"},
+    # profiles/scan_popc_1Mx768_b1_ncu.md
     ("scan_popc", 10_000_000, 768, 1, 100): {
-        "bytes": 1_920_232_704 + 3_361_024,
-        "sources_sha256": "e890e277990be005e25ae483e6b095740f046a384bb3505d9d70a40b46d91ae0"},
-    # profiles/scan_mma_packed_10Mx768_b16.md (DRAM capture of the 16-query command)
+        "bytes": 192_033_024 * 10 + 3_496_192,
+        "sources_sha256": "c8fee449e965c0380796eff6746723fcfc4d52b06a4c7d71314d8288f6dab996"},
+    # profiles/scan_mma_packed_10Mx768_b16.md
     ("scan_mma_packed", 10_000_000, 768, 16, 100): {
-        "bytes": 1_921_572_608 + 8_961_280,
-        "sources_sha256": "1e316739f7a77bb5621a34bb9e0487e4aa838e8cdbc4fbddf3b6f91390646617"},
+        "bytes": 193_664_000 * 10 + 9_467_904,
+        "sources_sha256": "875072a169888e57f774f9fe8663f2fd492a2b96b2553999bd6447552e06db74"},
 }
 
 
