@@ -878,7 +878,7 @@ def main():
             # MMA instructions per launch over the probe's instruction rate at this N
             key = "f8_m128_n64" if qn == 64 else "f8_m128_n16"
             cyc = tpeak[key]["cycles_per_mma"]
-            mmas = float((n + 127) // 128) * 2 * W       # 128-row tiles x K steps
+            mmas = float((n + 127) // 128) * W           # 128-row tiles x K steps (64 elements, e2m1)
             mhz = clocks.get("sm_mhz") or 2070.0
             floor_ms = mmas * cyc / sm_count / (mhz * 1e6) * 1e3
             roofline["mma_instruction_floor_ms"] = floor_ms

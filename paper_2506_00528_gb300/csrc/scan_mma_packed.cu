@@ -129,7 +129,9 @@ __host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn, int mod
     L.stage_bytes = pk_align((size_t)PK_ROWS * (2 * W + 2) * 8, 1024);
     L.b_off = L.stage_bytes * stages;
     const size_t states = (size_t)PK_EPI_WARPS * (qn / 2);
-    L.cand_off = L.b_off + (size_t)(W / 2) * qn * 128 * (mode ? 2 : 1);  // W/2 K-chunks of qn x 128 B
+    // mode 0: ceil(W/4) K-chunks of qn x 128 B (e2m1, 256 elements a chunk);
+    // mode 1: two operands of W/2 K-chunks (e4m3, 128 elements a chunk)
+    L.cand_off = L.b_off + (mode ? (size_t)(W / 2) * qn * 128 * 2 : (size_t)((W + 3) / 4) * qn * 128);
     L.scratch_off = L.cand_off + states * PK_CAP * (mode ? 8 : 4);  // one staged list per epilogue warp
     L.tau_off = L.scratch_off + (size_t)PK_EPI_WARPS * PK_STAGE_LIST_K * 8;
     L.thr_off = L.tau_off + states * 8;
@@ -144,6 +146,27 @@ __host__ __device__ inline PkLayout pk_layout(int W, int stages, int qn, int mod
 // Instruction descriptor: D = f32, A = B = e4m3, both K-major, M = 128, N = qn.
 __host__ __device__ constexpr uint32_t pk_idesc(int qn) {
     return (1u << 4) | ((uint32_t)(qn >> 3) << 17) | ((uint32_t)(PK_ROWS >> 4) << 24);
+}
+
+// Block-scaled fp4 (kind::mxf4): A = B = e2m1 (format 1), both K-major,
+// ue8m0 scale factors (bit 23), M = 128, N = qn.
+__host__ __device__ constexpr uint32_t pk_idesc_f4(int qn) {
+    return (1u << 7) | (1u << 10) | ((uint32_t)(qn >> 3) << 17) | (1u << 23) |
+           ((uint32_t)(PK_ROWS >> 4) << 24);
+}
+
+// D (TMEM) += A (TMEM) * B (shared memory descriptor), e2m1 operands with
+// the scale factors at TMEM addresses sfa, sfb.
+__device__ __forceinline__ void mma_f4_tmem_a(uint32_t dtmem, uint32_t atmem, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                              uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %6, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], [%1], %2, %3, [%4], "
+        "[%5], p;\n\t}" ::"r"(dtmem),
+        "r"(atmem), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
+        : "memory");
 }
 
 // D (TMEM) += A (TMEM) * B (shared memory descriptor).
@@ -161,6 +184,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_u32(bar))
+        : "memory");
+}
+
+// Store 16 consecutive 32-bit columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+        "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]),
+        "r"(v[15])
         : "memory");
 }
 
@@ -236,6 +270,22 @@ __device__ __forceinline__ void unpack_word(uint64_t p, uint64_t m, uint32_t* o)
     unpack_half((uint32_t)(nz >> 32), (uint32_t)(m >> 32), o + 8);
 }
 
+// e2m1 TMEM columns of one 64-bit word pair (64 dimensions, 8 columns of 8
+// nibbles).  The database element is +2 (0x4) or -2 (0xC): nibble bit 2 =
+// non-zero, bit 3 = sign.  K order: column 4h + c (h = the word's 32-bit
+// half), nibble i holds dimension 32h + c + 4i, so a column is two shifts
+// and masks of each plane.
+__device__ __forceinline__ void unpack_word_f4(uint64_t p, uint64_t m, uint32_t* o) {
+    const uint64_t nz = p | m;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const uint32_t z = (uint32_t)(nz >> (32 * h)), g = (uint32_t)(m >> (32 * h));
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            o[4 * h + c] = (((z >> c) & 0x11111111u) << 2) | (((g >> c) & 0x11111111u) << 3);
+    }
+}
+
 // Candidate key -> list key.  Mode 0: (Delta/2 << 20 | row - row0), a
 // uint32, -> (Delta << 32 | row).  Mode 1: (score key << 20 | row - row0), a
 // uint64, -> (score key << 32 | row).
@@ -309,7 +359,15 @@ template <int QN, int MODE>
 __global__ void __launch_bounds__(PK_THREADS, 1)
 scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a) {
     using CandT = std::conditional_t<MODE == 0, uint32_t, uint64_t>;
-    constexpr uint32_t IDESC = pk_idesc(QN);
+    // mode 0: e2m1 operands (kind::mxf4, unit scale factors, K = 64 a step);
+    // mode 1: e4m3 (kind::f8f6f4, K = 32 a step; the split int8 query parts
+    // need e4m3's range)
+    constexpr bool F4 = MODE == 0;
+    constexpr uint32_t IDESC = F4 ? pk_idesc_f4(QN) : pk_idesc(QN);
+    constexpr int ACOLS = F4 ? 8 * PK_W_MAX : PK_A_COLS;   // TMEM columns of one A buffer
+    constexpr int DCOL0 = 2 * ACOLS;                        // accumulators after the A buffers
+    constexpr uint32_t SFCOL = DCOL0 + 2 * PK_QN_MAX;       // mode 0: scale factors (32 columns)
+    static_assert(!F4 || SFCOL + 32 <= PK_TMEM_COLS, "TMEM columns");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -347,7 +405,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
     const int ntl = tile_end > tile0 ? (int)(tile_end - tile0) : 0;
     const int64_t row0 = tile0 * PK_ROWS;
     const int npairs = W / 2;
-    const int ksteps = 2 * W;  // K = 64 W bytes, 32 per MMA
+    const int ksteps = F4 ? W : 2 * W;  // K = 64 W elements: 64 per e2m1 step, 32 per e4m3 step
     const uint32_t tile_bytes = (uint32_t)(PK_ROWS * a.pitch * 8);
 
     if (tid == 0) {
@@ -367,7 +425,34 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
     }
     // Query operand: 16-byte units of K-major SWIZZLE_128B rows (the 16-byte
     // unit u of row n of a 128-byte chunk sits at unit u ^ (n % 8)).
-    {
+    if constexpr (F4) {
+        // mode 0: e2m1 nibbles, +1 = 0x2, -1 = 0xA, 32 elements a 16-byte
+        // unit; K position 64 w + 32 h + 8 c + i holds dimension
+        // 64 w + 32 h + c + 4 i (the database's column order)
+        const int units_per_row = 8 * ((W + 3) / 4);  // whole 128-byte chunks
+        for (int i = tid; i < QN * units_per_row; i += PK_THREADS) {
+            const int n = i / units_per_row, ku = i - n * units_per_row;
+            const int kb0 = ku * 32;  // first K element of the unit
+            uint32_t o[4] = {0u, 0u, 0u, 0u};
+            const int w = kb0 >> 6;
+            if (n < a.nqg && w < W) {
+                const uint64_t p = a.Q[(int64_t)n * 2 * W + w];
+                const uint64_t m = a.Q[(int64_t)n * 2 * W + W + w];
+                const int h = (kb0 >> 5) & 1;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const int bit = 32 * h + (e >> 3) + 4 * (e & 7);
+                    const uint32_t nib = ((p >> bit) & 1u) ? 0x2u : (((m >> bit) & 1u) ? 0xAu : 0u);
+                    o[e >> 3] |= nib << (4 * (e & 7));
+                }
+            }
+            const int c = kb0 >> 8, uc = (kb0 & 255) >> 5;
+            uint8_t* dst = qop + (size_t)c * QN * 128 + (n >> 3) * 1024 + (n & 7) * 128 +
+                           ((uc ^ (n & 7)) << 4);
+            *reinterpret_cast<uint4*>(dst) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+        fence_proxy_async_smem();  // generic-proxy writes read by the tensor core
+    } else {
         const int units_per_row = 4 * W;  // 64 W bytes / 16
         for (int i = tid; i < QN * units_per_row; i += PK_THREADS) {
             const int n = i / units_per_row, ku = i - n * units_per_row;
@@ -494,16 +579,25 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(PK_D_COL0 + b * QN);
-                const uint32_t at = tmem_base + (uint32_t)(b * PK_A_COLS);
-                mma_f8_tmem_a(dt, at, bd[0], IDESC, 0u);
-                if constexpr (MODE == 1) mma_f8_tmem_a(dt, at, bd[0] + lo_off, IDESC, 1u);
+                const uint32_t dt = tmem_base + (uint32_t)(DCOL0 + b * QN);
+                const uint32_t at = tmem_base + (uint32_t)(b * ACOLS);
+                if constexpr (F4) {
+                    // one K step of 64 elements = 8 TMEM columns of A, 32 B of B
+                    const uint32_t sfa = tmem_base + SFCOL, sfb = tmem_base + SFCOL + 8u;
+                    mma_f4_tmem_a(dt, at, bd[0], IDESC, sfa, sfb, 0u);
 #pragma unroll
-                for (int kk = 1; kk < 2 * PK_W_MAX; ++kk) {
-                    if (kk < ksteps) {
-                        mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk], IDESC, 1u);
-                        if constexpr (MODE == 1)
+                    for (int kk = 1; kk < PK_W_MAX; ++kk)
+                        if (kk < ksteps)
+                            mma_f4_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk], IDESC, sfa, sfb, 1u);
+                } else {
+                    mma_f8_tmem_a(dt, at, bd[0], IDESC, 0u);
+                    mma_f8_tmem_a(dt, at, bd[0] + lo_off, IDESC, 1u);
+#pragma unroll
+                    for (int kk = 1; kk < 2 * PK_W_MAX; ++kk) {
+                        if (kk < ksteps) {
+                            mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk], IDESC, 1u);
                             mma_f8_tmem_a(dt, at + (uint32_t)(8 * kk), bd[kk] + lo_off, IDESC, 1u);
+                        }
                     }
                 }
                 mma_commit(&d_full[b]);  // one commit per tile: each drains the MMA pipe
@@ -518,6 +612,15 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
         const int h = warp >> 2;               // word pairs h, h + 2, ... of the row
         const int r = (warp & 3) * 32 + lane;  // row in the tile = TMEM lane
         const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+        if (F4 && h == 0) {
+            // mode 0: unit scale factors (ue8m0 2^0) for every lane, written
+            // before this warp's first A buffer (so before any MMA)
+            uint32_t o[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) o[c] = 0x7F7F7F7Fu;
+            tmem_st32(tmem_base + lane_off + SFCOL, o);
+            tmem_wait_st();
+        }
         for (int t = 0; t < ntl; ++t) {
             const int s = t % S, b = t & 1;
             int got = 1;
@@ -551,15 +654,22 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
                 break;
             }
             tc_fence_after();
-            const uint32_t abase = tmem_base + lane_off + (uint32_t)(b * PK_A_COLS);
+            const uint32_t abase = tmem_base + lane_off + (uint32_t)(b * ACOLS);
 #pragma unroll
             for (int i = 0; i < PK_W_MAX / 4; ++i) {
                 const int pi = h + 2 * i;
                 if (pi < npairs) {
-                    uint32_t o[32];
-                    unpack_word(pw[i].x, mw[i].x, o);
-                    unpack_word(pw[i].y, mw[i].y, o + 16);
-                    tmem_st32(abase + (uint32_t)(32 * pi), o);
+                    if constexpr (F4) {  // word pair pi: columns 16 pi .. 16 pi + 15
+                        uint32_t o[16];
+                        unpack_word_f4(pw[i].x, mw[i].x, o);
+                        unpack_word_f4(pw[i].y, mw[i].y, o + 8);
+                        tmem_st16(abase + (uint32_t)(16 * pi), o);
+                    } else {
+                        uint32_t o[32];
+                        unpack_word(pw[i].x, mw[i].x, o);
+                        unpack_word(pw[i].y, mw[i].y, o + 16);
+                        tmem_st32(abase + (uint32_t)(32 * pi), o);
+                    }
                 }
             }
             tmem_wait_st();
@@ -649,7 +759,7 @@ scan_mma_packed_kernel(const __grid_constant__ CUtensorMap tmap, const PkArgs a)
             }
             tc_fence_after();
             uint32_t v[QH];
-            tmem_ld_wait<QH>(tmem_base + lane_off + (uint32_t)(PK_D_COL0 + b * QN + qbase), v);
+            tmem_ld_wait<QH>(tmem_base + lane_off + (uint32_t)(DCOL0 + b * QN + qbase), v);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&d_empty[b]);
