@@ -272,7 +272,7 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
 #define EVP_PATH_POPC 1
 #define EVP_PATH_MMA  2
 #define EVP_PATH_MMA_PACKED 3
-#define EVP_AUTO_POPC_MAX_NQ 3
+#define EVP_AUTO_POPC_MAX_NQ 2
 #define EVP_AUTO_PACKED_MAX_NQ 32
 #define EVP_AUTO_PACKED_MAX_NQ_NO_COPY 128
 #define EVP_MMA_MAX_K 1024
