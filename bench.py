@@ -156,8 +156,8 @@ MEASURED_TRAFFIC = {
         "sources_sha256": "c8fee449e965c0380796eff6746723fcfc4d52b06a4c7d71314d8288f6dab996"},
     # profiles/scan_mma_packed_10Mx768_b16.md
     ("scan_mma_packed", 10_000_000, 768, 16, 100): {
-        "bytes": 193_664_000 * 10 + 9_467_904,
-        "sources_sha256": "875072a169888e57f774f9fe8663f2fd492a2b96b2553999bd6447552e06db74"},
+        "bytes": 194_052_096 * 10 + 9_144_832,
+        "sources_sha256": "9bc6bbd1ea71a3206d7b033908286945a01661819dabb3283c55470b58cc0acd"},
 }
 
 
