@@ -119,7 +119,11 @@ __device__ __forceinline__ void pr_tmem_st32(uint32_t taddr, const uint32_t (&v)
 // the other three warps reading columns 256-511 of their TMEM lanes with
 // tcgen05.ld throughout (an epilogue draining the other accumulator), 6 the
 // switch of 4 without the restart (accumulate = 1 throughout), 7 the restart
-// of 4 without the switch (one accumulator, accumulate = 0 every 24).
+// of 4 without the switch (one accumulator, accumulate = 0 every 24); 8 the
+// scan's tile structure with run-time loops (per tile of three 4-instruction
+// chunks: a barrier test and fence per chunk, a commit per chunk, the
+// accumulator switch with accumulate = 0, a commit per tile), 9 the same
+// tile with its chunk loop unrolled and compile-time accumulate flags.
 template <int CG, int KIND, int AMODE, int EXTRA>
 __global__ void __launch_bounds__(PR_THREADS, 1)
 probe_mma_kernel(int fill, int64_t iters, uint32_t idesc, int64_t* cycles, int32_t* status) {
@@ -129,8 +133,8 @@ probe_mma_kernel(int fill, int64_t iters, uint32_t idesc, int64_t* cycles, int32
     uint8_t* A = smem;
     uint8_t* B = smem + PR_A_BYTES;
     uint64_t* done = reinterpret_cast<uint64_t*>(smem + PR_STAGES * PR_STAGE_BYTES);
-    uint64_t* spare = done + 1;  // EXTRA 1: commits; EXTRA 2: tested (complete) barrier
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 2);
+    uint64_t* spare = done + 1;  // EXTRA 1: commits; EXTRA 2, 8, 9: tested (complete) barrier
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 4);  // spare + 1, + 2: commits (8, 9)
     int* stop = reinterpret_cast<int*>(tmem_slot + 1);  // EXTRA 5: the issuer is done
     const int tid = threadIdx.x, warp = tid >> 5;
     const uint32_t rank = CG == 2 ? pr_cluster_rank() : 0u;
@@ -165,8 +169,10 @@ probe_mma_kernel(int fill, int64_t iters, uint32_t idesc, int64_t* cycles, int32
         *stop = 0;
         mbar_init(done, 1);
         mbar_init(spare, 1);
+        mbar_init(spare + 1, 1);
+        mbar_init(spare + 2, 1);
         fence_mbar_init();
-        if (EXTRA == 2) mbar_arrive(spare);  // phase 0 complete
+        if (EXTRA == 2 || EXTRA == 8 || EXTRA == 9) mbar_arrive(spare);  // phase 0 complete
     }
     fence_proxy_async_smem();
     if (warp == 0) {
@@ -232,10 +238,58 @@ probe_mma_kernel(int fill, int64_t iters, uint32_t idesc, int64_t* cycles, int32
         pr_mma<CG, KIND, AMODE, 1>(tmem, a + 2 * as, b0 + 4, idesc);
         pr_mma<CG, KIND, AMODE, 1>(tmem, a + 3 * as, b0 + 6, idesc);
         int extra_ok = 1;
+        if constexpr (EXTRA == 8 || EXTRA == 9) {
+            // tiles of three chunks of four instructions, accumulators at
+            // columns 0 and 256; every barrier involved is already complete
+            int ok8 = 1;
+            for (int64_t i = 4, tile = 0; i < iters; i += 12, ++tile) {
+                const uint32_t dt = tmem + ((uint32_t)(tile & 1) << 8);
+                ok8 &= mbar_try_wait(spare, 0) ? 1 : 0;
+                tc_fence_after();
+                if constexpr (EXTRA == 8) {
+#pragma unroll 1
+                    for (int kc = 0; kc < 3; ++kc) {
+                        ok8 &= mbar_try_wait(spare, 0) ? 1 : 0;
+                        tc_fence_after();
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if (kc > 0 || kk > 0)
+                                pr_mma<CG, KIND, AMODE, 1>(dt, a + kk * as, b0 + 2 * kk, idesc);
+                            else
+                                pr_mma<CG, KIND, AMODE, 0>(dt, a + kk * as, b0 + 2 * kk, idesc);
+                        }
+                        if constexpr (CG == 1)
+                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(spare + 1)) : "memory");
+                        else
+                            asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(spare + 1)) : "memory");
+                    }
+                } else {
+#pragma unroll
+                    for (int kc = 0; kc < 3; ++kc) {
+                        ok8 &= mbar_try_wait(spare, 0) ? 1 : 0;
+                        tc_fence_after();
+                        if (kc == 0) pr_mma<CG, KIND, AMODE, 0>(dt, a, b0, idesc);
+                        else pr_mma<CG, KIND, AMODE, 1>(dt, a, b0, idesc);
+                        pr_mma<CG, KIND, AMODE, 1>(dt, a + as, b0 + 2, idesc);
+                        pr_mma<CG, KIND, AMODE, 1>(dt, a + 2 * as, b0 + 4, idesc);
+                        pr_mma<CG, KIND, AMODE, 1>(dt, a + 3 * as, b0 + 6, idesc);
+                        if constexpr (CG == 1)
+                            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(spare + 1)) : "memory");
+                        else
+                            asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(spare + 1)) : "memory");
+                    }
+                }
+                if constexpr (CG == 1)
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(spare + 2)) : "memory");
+                else
+                    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(spare + 2)) : "memory");
+            }
+            if (!ok8) report(status, EVP_ERR_INVALID);
+        }
         uint64_t so = 0;  // EXTRA 3: start-address offset of the current buffer (16-byte units)
         uint32_t dcur = tmem;  // EXTRA 4: current accumulator
         int nacc = 4;          // EXTRA 4: instructions into it so far
-        for (int64_t i = 4; i < iters; i += 4) {
+        for (int64_t i = 4; i < ((EXTRA == 8 || EXTRA == 9) ? 0 : iters); i += 4) {
             if constexpr (EXTRA == 4 || EXTRA == 6 || EXTRA == 7) {
                 if (nacc == 24) {
                     if (EXTRA != 7) dcur ^= 256u;
@@ -346,7 +400,7 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
     const int cg = cta_pair ? 2 : 1;
     const int fill = (kind >> 8) & 3;  // operand values (see evp.h)
     const bool tmem_a = (kind >> 10) & 1, m64 = (kind >> 11) & 1;
-    const int extra = (kind >> 12) & 7;  // per-four-MMA extra work (see the kernel)
+    const int extra = (kind >> 12) & 15;  // per-four-MMA extra work (see the kernel)
     kind &= 0xff;
     if ((kind != 0 && kind != 1 && kind != 2) || fill == 3 || (fill == 2 && kind != 0) || n < 16 ||
         n > 256 ||
@@ -356,7 +410,7 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
     if (m64 && cg != 1) return EVP_ERR_INVALID;
     if (tmem_a && (m64 || kind != 0 || fill == 2 || n > 128)) return EVP_ERR_INVALID;
     if (m64 && n % 8 != 0) return EVP_ERR_INVALID;
-    if (extra != 0 && (tmem_a || kind != 0)) return EVP_ERR_INVALID;
+    if (extra > 9 || (extra != 0 && (tmem_a || kind != 0))) return EVP_ERR_INVALID;
     if (kind == 2 && (tmem_a || m64 || fill != 0)) return EVP_ERR_INVALID;
     if (extra >= 4 && n > 256) return EVP_ERR_INVALID;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -397,7 +451,9 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
                                                  : (extra == 5 ? probe_mma_kernel<1, 0, 0, 5>
                                                  : (extra == 6 ? probe_mma_kernel<1, 0, 0, 6>
                                                  : (extra == 7 ? probe_mma_kernel<1, 0, 0, 7>
-                                                               : probe_mma_kernel<1, 0, 0, 0>))))))));
+                                                 : (extra == 8 ? probe_mma_kernel<1, 0, 0, 8>
+                                                 : (extra == 9 ? probe_mma_kernel<1, 0, 0, 9>
+                                                               : probe_mma_kernel<1, 0, 0, 0>))))))))));
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    PR_SMEM_LAUNCH);
         if (err == cudaSuccess) {
@@ -418,7 +474,9 @@ int32_t evp_probe_tensor_rate(int32_t kind, int32_t cta_pair, int32_t n, int64_t
                                                  : (extra == 5 ? probe_mma_kernel<2, 0, 0, 5>
                                                  : (extra == 6 ? probe_mma_kernel<2, 0, 0, 6>
                                                  : (extra == 7 ? probe_mma_kernel<2, 0, 0, 7>
-                                                               : probe_mma_kernel<2, 0, 0, 0>))))))));
+                                                 : (extra == 8 ? probe_mma_kernel<2, 0, 0, 8>
+                                                 : (extra == 9 ? probe_mma_kernel<2, 0, 0, 9>
+                                                               : probe_mma_kernel<2, 0, 0, 0>))))))))));
         err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    PR_SMEM_LAUNCH);
         if (err == cudaSuccess) {

@@ -56,6 +56,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 namespace evp {
@@ -66,6 +67,7 @@ constexpr int MMA_M = 128;   // query rows per CTA (= TMEM lanes)
 constexpr int MMA_N = MMA_TILE_ROWS;  // database rows per accumulator tile (240)
 constexpr int KSTEP = 32;    // bytes of K per instruction (64 fp4 elements)
 constexpr int KCHUNK = 128;  // bytes of K per stage (256 elements)
+constexpr int MMA_KCHUNK_MAX = 4;  // chunks per row: d <= 1024
 constexpr int EPI_GROUPS = (MMA_N + 31) / 32;  // 32-column TMEM loads per tile (the last: 16 columns)
 static_assert(EPI_GROUPS % 2 == 0, "the epilogue loads groups in pairs");
 static_assert(MMA_N % 16 == 0 && MMA_N > 224 && MMA_N <= 256, "N of the instruction, last group");
@@ -522,36 +524,52 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             const uint32_t sfa = tmem_base + SF_COL, sfb = tmem_base + SF_COL + 8u;
             int it = 0, tt = 0;
             bool ok = true;
+            // One item's tiles with the chunk loop unrolled for its chunk
+            // count: the issuing thread's control flow between MMAs costs
+            // tensor time (the probe: a tile of three 4-instruction chunks
+            // issued by a run-time loop takes 138 clocks per instruction at
+            // N = 240, unrolled 120, the instruction's own), so a tile's
+            // MMAs, waits and commits are straight-line code; a wait that is
+            // not already complete goes to the bounded slow path.
+            auto issue_item = [&](auto kch_c, int ntiles) {
+                constexpr int KCH = decltype(kch_c)::value;
+                for (int t = 0; t < ntiles; ++t, ++tt) {
+                    const int b = tt & 1;
+                    const uint32_t use = (uint32_t)(tt >> 1);
+                    if (!mbar_try_wait(&acc_empty[b], (use & 1u) ^ 1u) &&
+                        !mbar_wait_or_abort(&acc_empty[b], (use & 1u) ^ 1u, abort_flag))
+                        return false;
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)(b * MMA_N);
+#pragma unroll
+                    for (int kc = 0; kc < KCH; ++kc, ++it) {
+                        const int s = it % STAGES;
+                        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                        if (!mbar_try_wait(&full[s], ph) &&
+                            !mbar_wait_or_abort(&full[s], ph, abort_flag))
+                            return false;
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
+                        const uint32_t sb = sa + A_STAGE_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < KCHUNK / KSTEP; ++kk) {
+                            mma_f4<CG>(dt, sw128_desc(sa + kk * KSTEP), sw128_desc(sb + kk * KSTEP),
+                                       sfa, sfb, (kc > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        mma_commit_all<CG>(&empty[s]);
+                    }
+                    mma_commit_all<CG>(&acc_full[b]);
+                }
+                return true;
+            };
+            static_assert(MMA_KCHUNK_MAX == 4, "chunk counts 1-4 instantiated");
             for (int item = worker; item < nitems && ok; item += nworkers) {
               const Item w = item_of(item);
-              const int kchunks = args_of(w.b).kchunks;
-              for (int t = 0; t < w.ntiles && ok; ++t, ++tt) {
-                const int b = tt & 1;
-                const uint32_t use = (uint32_t)(tt >> 1);
-                if (!mbar_wait_or_abort(&acc_empty[b], (use & 1u) ^ 1u, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(b * MMA_N);
-                for (int kc = 0; kc < kchunks; ++kc, ++it) {
-                    const int s = it % STAGES;
-                    const uint32_t ph = (uint32_t)((it / STAGES) & 1);
-                    if (!mbar_wait_or_abort(&full[s], ph, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
-                    const uint32_t sb = sa + A_STAGE_BYTES;
-#pragma unroll
-                    for (int kk = 0; kk < KCHUNK / KSTEP; ++kk) {
-                        mma_f4<CG>(dt, sw128_desc(sa + kk * KSTEP), sw128_desc(sb + kk * KSTEP),
-                                   sfa, sfb, (kc > 0 || kk > 0) ? 1u : 0u);
-                    }
-                    mma_commit_all<CG>(&empty[s]);
-                }
-                if (ok) mma_commit_all<CG>(&acc_full[b]);
+              switch (args_of(w.b).kchunks) {
+                case 1: ok = issue_item(std::integral_constant<int, 1>{}, w.ntiles); break;
+                case 2: ok = issue_item(std::integral_constant<int, 2>{}, w.ntiles); break;
+                case 3: ok = issue_item(std::integral_constant<int, 3>{}, w.ntiles); break;
+                default: ok = issue_item(std::integral_constant<int, 4>{}, w.ntiles); break;
               }
             }
             if (!ok) {
