@@ -88,21 +88,32 @@ constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
 constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
 constexpr int UBOUND_BYTES = MMA_M * 8;             // helper -> epilogue thresholds
 
-// CG = CTAs per tensor-core instruction.  CG = 1: M = 128, each CTA stages
-// its query tile and the whole 256-row database tile.  CG = 2: a CTA pair
-// (cluster of two) runs M = 256, N = 256 instructions issued by the even
-// CTA; each CTA stages its own 128 query rows and one half (128 rows) of
-// the database tile, and holds the accumulator rows of its own queries in
-// its TMEM.  The pair moves a third less operand data per flop through
-// L2 and shared memory.
+// Shared memory outside the operand pool: alignment slack, heaps, staging,
+// thresholds, barriers and flags.
+constexpr int SMEM_FIXED = 1024 + HEAP_BYTES + STAGING_BYTES + UBOUND_BYTES + 256;
+// Operand pool: the work item's query tile (kchunks x 16 KB, resident for
+// all of the item's database tiles) followed by the database stages.
+constexpr int POOL_BYTES = (232448 - SMEM_FIXED) / 1024 * 1024;
+constexpr int MAX_STAGES = 8;
+
+// CG = CTAs per tensor-core instruction.  CG = 1: M = 128, each CTA holds
+// its query tile and stages the whole 240-row database tile.  CG = 2: a CTA
+// pair (cluster of two) runs M = 256, N = 240 instructions issued by the
+// even CTA; each CTA holds its own 128 query rows and stages one half (120
+// rows) of the database tile, and holds the accumulator rows of its own
+// queries in its TMEM.  The query tile is loaded once per work item: per
+// database tile only the database rows move through L2 and shared memory.
 template <int CG>
 struct MmaCfg {
     static constexpr int B_ROWS = MMA_N / CG;  // database rows staged per CTA
-    static constexpr int B_STAGE_BYTES = B_ROWS * KCHUNK;
-    static constexpr int STAGE_BYTES = A_STAGE_BYTES + B_STAGE_BYTES;
-    static constexpr int STAGES = CG == 2 ? 4 : 3;
-    static constexpr size_t SMEM_BYTES = 1024 + (size_t)STAGES * STAGE_BYTES + HEAP_BYTES +
-                                         STAGING_BYTES + UBOUND_BYTES + 256;
+    static constexpr int STAGE_BYTES = B_ROWS * KCHUNK;
+    static constexpr size_t SMEM_BYTES = (size_t)SMEM_FIXED + POOL_BYTES;
+    // database stages that fit beside a query tile of a_chunks chunks
+    static constexpr int stages_for(int a_chunks) {
+        return (POOL_BYTES - a_chunks * A_STAGE_BYTES) / STAGE_BYTES < MAX_STAGES
+                   ? (POOL_BYTES - a_chunks * A_STAGE_BYTES) / STAGE_BYTES
+                   : MAX_STAGES;
+    }
     // Instruction descriptor of the block-scaled kinds: A = B = e2m1
     // (format 1 of kind::mxf4), both K-major, N = 240, scale factors ue8m0
     // (bit 23), M = 128 x CG; scale-factor IDs 0.
@@ -111,6 +122,10 @@ struct MmaCfg {
 };
 static_assert(MmaCfg<1>::SMEM_BYTES <= 232448 && MmaCfg<2>::SMEM_BYTES <= 232448,
               "shared memory per CTA");
+static_assert(MmaCfg<1>::stages_for(MMA_KCHUNK_MAX) >= 2 && MmaCfg<2>::stages_for(MMA_KCHUNK_MAX) >= 2,
+              "at least two database stages beside the largest query tile");
+static_assert(MmaCfg<1>::STAGE_BYTES % 1024 == 0 && MmaCfg<2>::STAGE_BYTES % 1024 == 0 &&
+              A_STAGE_BYTES % 1024 == 0, "128-byte swizzle atoms stay 1024-byte aligned");
 
 struct MmaArgs {
     int nq;
@@ -132,6 +147,10 @@ struct MmaArgs {
     int hist_bins;         // 2x + 1
     int32_t* status;
     int stall_fills;       // testing: CTA 0's producer stops after this many fills (-1: never)
+    // launch-wide (the multi-batch form reads them from the launch's own
+    // arguments): query-tile chunks reserved in shared memory (the largest
+    // kchunks of the launch) and the database stages beside them
+    int a_chunks, nstages;
 };
 
 // Multi-batch form (the batched plan's fused scan): one persistent launch
@@ -330,29 +349,36 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ MmaArgs a, const MmaMulti* __restrict__ multi) {
     using C = MmaCfg<CG>;
-    constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
+    // database stages (launch-wide: the stage ring runs on across items)
+    const int nst = a.nstages;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
-    uint8_t* stages = smem;
-    uint32_t* heap = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES);
-    uint32_t* staging = reinterpret_cast<uint32_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES);
-    uint64_t* ubound = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES +
+    uint8_t* qtile = smem;  // the item's query rows, [a_chunks][128 rows][128 B], swizzled
+    uint8_t* stages = smem + a.a_chunks * A_STAGE_BYTES;
+    uint32_t* heap = reinterpret_cast<uint32_t*>(smem + POOL_BYTES);
+    uint32_t* staging = reinterpret_cast<uint32_t*>(smem + POOL_BYTES + HEAP_BYTES);
+    uint64_t* ubound = reinterpret_cast<uint64_t*>(smem + POOL_BYTES + HEAP_BYTES +
                                                    STAGING_BYTES);  // [MMA_M]: item << 32 | T
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES + HEAP_BYTES +
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + POOL_BYTES + HEAP_BYTES +
                                                  STAGING_BYTES + UBOUND_BYTES);
-    uint64_t* full = bars;                 // [STAGES]
-    uint64_t* empty = bars + STAGES;       // [STAGES]
-    uint64_t* acc_full = bars + 2 * STAGES;      // [2]
-    uint64_t* acc_empty = bars + 2 * STAGES + 2; // [2]
-    uint64_t* done = bars + 2 * STAGES + 4;      // [1]
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+    uint64_t* full = bars;                       // [MAX_STAGES]
+    uint64_t* empty = bars + MAX_STAGES;         // [MAX_STAGES]
+    uint64_t* acc_full = bars + 2 * MAX_STAGES;      // [2]
+    uint64_t* acc_empty = bars + 2 * MAX_STAGES + 2; // [2]
+    uint64_t* done = bars + 2 * MAX_STAGES + 4;      // [1]
+    uint64_t* q_full = bars + 2 * MAX_STAGES + 5;    // [1] the item's query tile landed
+    uint64_t* q_empty = bars + 2 * MAX_STAGES + 6;   // [1] the item's MMAs completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 7);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
     int* cur_item = abort_flag + 1;   // item the epilogue is on
     int* epi_done = abort_flag + 2;   // epilogue finished (helper stops)
     int* fills = abort_flag + 3;      // stage fills this CTA's producer issued
     int* peer_fills = abort_flag + 4; // CG = 2: the same count of the other CTA
+    int* qfills = abort_flag + 5;     // query tiles this CTA's producer loaded
+    int* peer_qfills = abort_flag + 6;
+    static_assert((2 * MAX_STAGES + 7) * 8 + 4 + 7 * 4 <= 256, "barriers and flags");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // CTA pair: rank 0 issues the MMAs; both run every other role.
@@ -399,7 +425,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     };
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -408,11 +434,15 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             mbar_init(&acc_empty[b], CG * EPI_WARPS);  // one arrival per epilogue warp
         }
         mbar_init(done, 1);
+        mbar_init(q_full, 1);
+        mbar_init(q_empty, 1);
         *abort_flag = 0;
         *cur_item = -1;
         *epi_done = 0;
         *fills = 0;
         *peer_fills = 0;
+        *qfills = 0;
+        *peer_qfills = 0;
         fence_mbar_init();
     }
     for (int i = threadIdx.x; i < MMA_M; i += NUM_THREADS) ubound[i] = ~0ull;
@@ -453,11 +483,12 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     if (warp == 0) {
         if (lane == 0) {
             // ---------------- TMA producer ----------------
-            // CG = 2: both CTAs' copies are counted on the leader's full
-            // barrier, which expects the bytes of the pair.
-            int it = 0;
+            // CG = 2: both CTAs' copies are counted on the leader's
+            // barriers, which expect the bytes of the pair.
+            int it = 0, s = 0, qi = 0;
+            uint32_t ph = 0;
             bool ok = true;
-            for (int item = worker; item < nitems && ok; item += nworkers) {
+            for (int item = worker; item < nitems && ok; item += nworkers, ++qi) {
                 const Item w = item_of(item);
                 const MmaArgs& a = args_of(w.b);
                 const int kchunks = a.kchunks;
@@ -469,11 +500,27 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 }
                 // a tile past the last query (odd tile count) loads tile 0; its rows are ignored
                 const int32_t arow = w.qt < a.qtiles ? w.qt * a.qa : 0;
+                // the item's query tile, once the previous item's MMAs have
+                // read theirs
+                if (!mbar_wait_or_abort(q_empty, (uint32_t)(qi & 1) ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t qbytes = (uint32_t)(kchunks * A_STAGE_BYTES);
+                if constexpr (CG == 1) {
+                    mbar_arrive_expect_tx(q_full, qbytes);
+                    for (int kc = 0; kc < kchunks; ++kc)
+                        tma_load_2d(qtile + kc * A_STAGE_BYTES, mapA, q_full, kc * KCHUNK, arow);
+                } else {
+                    if (leader) mbar_arrive_expect_tx(q_full, 2 * qbytes);
+                    const uint32_t qb = peer_addr(q_full, 0u);
+                    for (int kc = 0; kc < kchunks; ++kc)
+                        tma_load_2d_pair(qtile + kc * A_STAGE_BYTES, mapA, qb, kc * KCHUNK, arow);
+                }
+                *qfills = qi + 1;
                 for (int t = 0; t < w.ntiles && ok; ++t) {
                     const int32_t brow = (int32_t)(w.row0 + (int64_t)t * MMA_N + rank * C::B_ROWS);
                     for (int kc = 0; kc < kchunks; ++kc, ++it) {
-                        const int s = it % STAGES;
-                        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
                         if (it == a.stall_fills && blockIdx.x == 0) {
                             // testing: a producer that stops issuing copies, so
                             // that the consumers' bounded waits expire
@@ -491,13 +538,14 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                         uint8_t* st = stages + s * STAGE_BYTES;
                         if constexpr (CG == 1) {
                             mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                            tma_load_2d(st, mapA, &full[s], kc * KCHUNK, arow);
-                            tma_load_2d(st + A_STAGE_BYTES, mapB, &full[s], kc * KCHUNK, brow);
+                            tma_load_2d(st, mapB, &full[s], kc * KCHUNK, brow);
                         } else {
                             if (leader) mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
-                            const uint32_t fb = peer_addr(&full[s], 0u);
-                            tma_load_2d_pair(st, mapA, fb, kc * KCHUNK, arow);
-                            tma_load_2d_pair(st + A_STAGE_BYTES, mapB, fb, kc * KCHUNK, brow);
+                            tma_load_2d_pair(st, mapB, peer_addr(&full[s], 0u), kc * KCHUNK, brow);
+                        }
+                        if (++s == nst) {
+                            s = 0;
+                            ph ^= 1u;
                         }
                     }
                 }
@@ -505,8 +553,8 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             if (ok) {
                 // the MMAs have read every stage filled (and, for a pair, the
                 // leader's releases of them have all arrived here)
-                for (int j = max(0, it - STAGES); j < it && ok; ++j)
-                    ok = mbar_wait_or_abort(&empty[j % STAGES], (uint32_t)((j / STAGES) & 1),
+                for (int j = max(0, it - nst); j < it && ok; ++j)
+                    ok = mbar_wait_or_abort(&empty[j % nst], (uint32_t)((j / nst) & 1),
                                             abort_flag);
             }
             if (!ok) {
@@ -522,7 +570,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // the instruction reads the same offsets in the peer CTA (and
             // the scale factors at the same TMEM columns).
             const uint32_t sfa = tmem_base + SF_COL, sfb = tmem_base + SF_COL + 8u;
-            int it = 0, tt = 0;
+            const uint32_t qa0 = smem_u32(qtile), sb0 = smem_u32(stages);
+            int s = 0, tt = 0, qi = 0;
+            uint32_t ph = 0;
             bool ok = true;
             // One item's tiles with the chunk loop unrolled for its chunk
             // count: the issuing thread's control flow between MMAs costs
@@ -533,6 +583,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // not already complete goes to the bounded slow path.
             auto issue_item = [&](auto kch_c, int ntiles) {
                 constexpr int KCH = decltype(kch_c)::value;
+                if (!mbar_wait_or_abort(q_full, (uint32_t)(qi & 1), abort_flag)) return false;
                 for (int t = 0; t < ntiles; ++t, ++tt) {
                     const int b = tt & 1;
                     const uint32_t use = (uint32_t)(tt >> 1);
@@ -542,24 +593,28 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     tc_fence_after();
                     const uint32_t dt = tmem_base + (uint32_t)(b * MMA_N);
 #pragma unroll
-                    for (int kc = 0; kc < KCH; ++kc, ++it) {
-                        const int s = it % STAGES;
-                        const uint32_t ph = (uint32_t)((it / STAGES) & 1);
+                    for (int kc = 0; kc < KCH; ++kc) {
                         if (!mbar_try_wait(&full[s], ph) &&
                             !mbar_wait_or_abort(&full[s], ph, abort_flag))
                             return false;
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(stages + s * STAGE_BYTES);
-                        const uint32_t sb = sa + A_STAGE_BYTES;
+                        const uint32_t sa = qa0 + (uint32_t)(kc * A_STAGE_BYTES);
+                        const uint32_t sb = sb0 + (uint32_t)(s * STAGE_BYTES);
 #pragma unroll
                         for (int kk = 0; kk < KCHUNK / KSTEP; ++kk) {
                             mma_f4<CG>(dt, sw128_desc(sa + kk * KSTEP), sw128_desc(sb + kk * KSTEP),
                                        sfa, sfb, (kc > 0 || kk > 0) ? 1u : 0u);
                         }
                         mma_commit_all<CG>(&empty[s]);
+                        const bool wrap = s + 1 == nst;
+                        s = wrap ? 0 : s + 1;
+                        ph ^= wrap ? 1u : 0u;
                     }
                     mma_commit_all<CG>(&acc_full[b]);
                 }
+                // the query tile is free once the item's MMAs complete
+                mma_commit_all<CG>(q_empty);
+                ++qi;
                 return true;
             };
             static_assert(MMA_KCHUNK_MAX == 4, "chunk counts 1-4 instantiated");
@@ -835,30 +890,50 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     tc_fence_before();
     __syncthreads();
     if constexpr (CG == 2) {
-        // each CTA tells the other how many stage fills its producer issued
-        if (threadIdx.x == 0) st_cluster_u32(peer_addr(peer_fills, rank ^ 1u), (uint32_t)*fills);
+        // each CTA tells the other how many stage fills and query tiles its
+        // producer issued
+        if (threadIdx.x == 0) {
+            st_cluster_u32(peer_addr(peer_fills, rank ^ 1u), (uint32_t)*fills);
+            st_cluster_u32(peer_addr(peer_qfills, rank ^ 1u), (uint32_t)*qfills);
+        }
         cluster_sync_all();
     }
     if (*(volatile int*)abort_flag && threadIdx.x == 0 && leader) {
         // After an abort, copies issued into either CTA's stages may still be
         // in flight; every copy of fill j signals the leader's full barrier
-        // of stage j % STAGES.  A fill could only be issued once the fill
-        // STAGES before it had completed, so only the last STAGES fills of
-        // the two producers can be pending: wait (bounded) for each of them,
-        // first completing the accounting of a fill that one CTA of the pair
+        // of stage j % nst.  A fill could only be issued once the fill nst
+        // before it had completed, so only the last nst fills of the two
+        // producers can be pending: wait (bounded) for each of them, first
+        // completing the accounting of a fill that one CTA of the pair
         // issued and the other did not (its expected bytes never come, or
         // its arrival never happened).  The MMA issuer has already waited
         // for every MMA it issued.
         const int own = *fills;
         const int other = CG == 2 ? *peer_fills : own;
         const int hi = max(own, other);
-        for (int j = max(0, hi - STAGES); j < hi; ++j) {
-            const int s = j % STAGES;
+        for (int j = max(0, hi - nst); j < hi; ++j) {
+            const int s = j % nst;
             if constexpr (CG == 2) {
                 if (j >= own) mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                 else if (j >= other) mbar_complete_tx(&full[s], STAGE_BYTES);
             }
-            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / STAGES) & 1))) break;
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / nst) & 1))) break;
+        }
+        // The same for the query tiles: a producer loads tile j only after
+        // the MMAs of item j - 1 completed, which waited for tile j - 1, so
+        // only the last one can be pending.
+        const int qown = *qfills;
+        const int qother = CG == 2 ? *peer_qfills : qown;
+        const int qhi = max(qown, qother);
+        if (qhi > 0) {
+            const int j = qhi - 1;
+            const uint32_t qbytes =
+                (uint32_t)(args_of(item_of(worker + j * nworkers).b).kchunks * A_STAGE_BYTES);
+            if constexpr (CG == 2) {
+                if (j >= qown) mbar_arrive_expect_tx(q_full, qbytes);
+                else if (j >= qother) mbar_complete_tx(q_full, qbytes);
+            }
+            mbar_wait_bounded(q_full, (uint32_t)(j & 1));
         }
     }
     __syncthreads();
@@ -1227,6 +1302,8 @@ int32_t run_mma_knn(const uint64_t* Q, int64_t nq, const uint8_t* S8, const uint
     args.hist_bins = hist_bins;
     args.status = status;
     args.stall_fills = take_stall_mma();
+    args.a_chunks = args.kchunks;
+    args.nstages = p.cg == 1 ? MmaCfg<1>::stages_for(args.a_chunks) : MmaCfg<2>::stages_for(args.a_chunks);
     const int items = (p.qtiles + p.cg - 1) / p.cg * p.nslices;
     if (p.cg == 1) {
         if (cudaFuncSetAttribute(scan_mma_kernel<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1338,6 +1415,7 @@ MultiLayout multi_layout(const MmaBatchSpec& b, int tiles_per_item) {
 
 struct MmaMultiPlan {
     int nb = 0, cg = 1, workers = 0;
+    int a_chunks = 1;  // the largest chunk count of the batches
     int64_t total_q = 0;
     size_t fm_smem = 0;
     MmaMulti* table = nullptr;   // device
@@ -1405,6 +1483,7 @@ int32_t mma_multi_create(const MmaBatchSpec* specs, int nb, MmaMultiPlan** out) 
         A.nq = (int)B.nq;
         A.ns = B.ns;
         A.kchunks = p.kp / KCHUNK;
+        P->a_chunks = std::max(P->a_chunks, A.kchunks);
         A.x = B.x;
         A.k = B.k;
         A.kunion = B.k;
@@ -1476,6 +1555,8 @@ int32_t mma_multi_run(MmaMultiPlan* P, int32_t* status, cudaStream_t stream) {
     MmaArgs a{};      // the launch's status word (the table's arguments hold the rest)
     a.status = status;
     a.stall_fills = -1;
+    a.a_chunks = P->a_chunks;
+    a.nstages = P->cg == 1 ? MmaCfg<1>::stages_for(a.a_chunks) : MmaCfg<2>::stages_for(a.a_chunks);
     CUtensorMap dummy;
     std::memset(&dummy, 0, sizeof(dummy));
     if (P->cg == 1) {
