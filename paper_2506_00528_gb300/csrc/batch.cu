@@ -34,7 +34,7 @@ namespace {
 constexpr int BRANCHES = 4;               // forked streams inside one run
 // Tile shapes tried for the fused scan, in k-chunk tiles per work item (an
 // item of a batch with kc 128-byte K chunks per row covers shape / kc
-// database tiles of 240 rows); 0 = each batch sliced in whole waves of the
+// database tiles of MMA_TILE_ROWS rows); 0 = each batch sliced in whole waves of the
 // persistent grid, as its own call would be.  Items must stay large: each
 // ends with a sort of its heaps and a k-key list per query, and every
 // list is merged at the end.

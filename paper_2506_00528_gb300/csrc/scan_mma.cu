@@ -15,9 +15,10 @@
 //
 // Kernel (persistent: one CTA per SM, or one CTA pair per two SMs, looping
 // over work items = (query tile, database slice)):
-//   warp 0      TMA producer: K-chunks of 128 bytes (256 elements) of the
-//               query tile (A, 128 x 128 B) and of the database tile (B,
-//               240 x 128 B, or its half for a CTA pair), SWIZZLE_128B,
+//   warp 0      TMA producer: the work item's query tile (A, 128 rows, all
+//               K, loaded once per item and kept in shared memory) and
+//               K-chunks of 128 bytes (256 elements) of the database tile
+//               (B, 240 x 128 B, or its half for a CTA pair), SWIZZLE_128B,
 //               through a ring of mbarrier stages;
 //   warp 1      allocates the 512 TMEM columns -- two accumulators of 240
 //               columns and the scale factors (32 columns of 2^0, written
@@ -65,13 +66,18 @@ namespace {
 
 constexpr int MMA_M = 128;   // query rows per CTA (= TMEM lanes)
 constexpr int MMA_N = MMA_TILE_ROWS;  // database rows per accumulator tile (240)
+// Accumulator tiles in tensor memory: the epilogue examines one while the
+// MMAs fill the other.  (Three tiles of 160 columns decouple the two sides
+// further, but the issuing thread's own time per 4-instruction chunk, ~540
+// clocks at any N, then exceeds the chunk's 320 clocks of tensor work: 240
+// columns in two tiles measured faster.)
+constexpr int NACC = 2;
 constexpr int KSTEP = 32;    // bytes of K per instruction (64 fp4 elements)
 constexpr int KCHUNK = 128;  // bytes of K per stage (256 elements)
 constexpr int MMA_KCHUNK_MAX = 4;  // chunks per row: d <= 1024
-constexpr int EPI_GROUPS = (MMA_N + 31) / 32;  // 32-column TMEM loads per tile (the last: 16 columns)
-static_assert(EPI_GROUPS % 2 == 0, "the epilogue loads groups in pairs");
-static_assert(MMA_N % 16 == 0 && MMA_N > 224 && MMA_N <= 256, "N of the instruction, last group");
-constexpr uint32_t SF_COL = 2 * MMA_N;  // scale factors: A at column 480, B at 488 (<= 8 each)
+constexpr int EPI_GROUPS = (MMA_N + 31) / 32;  // 32-column TMEM loads per tile
+static_assert(MMA_N % 16 == 0 && MMA_N >= 32 && MMA_N <= 256, "N of the instruction");
+constexpr uint32_t SF_COL = NACC * MMA_N;  // scale factors: A at column SF_COL, B 8 after (<= 8 each)
 constexpr int HEAP_SLOTS = 128 * 128;  // heap capacity: active queries x k <= 128 x 128
 constexpr int NUM_THREADS = 224;  // TMA, MMA, 4 epilogue warps, threshold helper
 constexpr int EPI_WARPS = 4;
@@ -84,6 +90,8 @@ constexpr int STAGING_BYTES = STAGE_SLOTS * MMA_M * 4;
 static_assert(STAGE_SLOTS >= 32, "staging must hold one full column group");
 constexpr uint32_t TMEM_COLS = 512;
 static_assert(SF_COL + 32 <= TMEM_COLS, "TMEM columns");
+static_assert((NACC - 1) * MMA_N + EPI_GROUPS * 32 <= (int)TMEM_COLS,
+              "the last tile's last 32-column load stays inside the allocation");
 constexpr int LOCAL_BITS = 20;  // row-in-slice bits of a heap key
 constexpr int64_t MAX_SLICE_ROWS = int64_t(1) << LOCAL_BITS;
 constexpr int UBOUND_BYTES = MMA_M * 8;             // helper -> epilogue thresholds
@@ -115,7 +123,7 @@ struct MmaCfg {
                    : MAX_STAGES;
     }
     // Instruction descriptor of the block-scaled kinds: A = B = e2m1
-    // (format 1 of kind::mxf4), both K-major, N = 240, scale factors ue8m0
+    // (format 1 of kind::mxf4), both K-major, N = MMA_N, scale factors ue8m0
     // (bit 23), M = 128 x CG; scale-factor IDs 0.
     static constexpr uint32_t IDESC = (1u << 7) | (1u << 10) | ((uint32_t)(MMA_N >> 3) << 17) |
                                       (1u << 23) | ((uint32_t)((MMA_M * CG) >> 4) << 24);
@@ -243,6 +251,86 @@ __device__ __forceinline__ void mma_commit_self(uint64_t* bar) {
     }
 }
 
+// The issuing thread's forms, on shared-memory addresses it keeps in
+// registers (no address arithmetic between the instructions).
+__device__ __forceinline__ bool mbar_try_wait_u32(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Non-blocking test of a phase (no suspension while it is incomplete).
+__device__ __forceinline__ bool mbar_test_wait_u32(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+template <int CG>
+__device__ __forceinline__ void mma_commit_all_u32(uint32_t bar) {
+    if constexpr (CG == 1) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+    } else {
+        const uint16_t both = 3;
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster"
+            ".b64 [%0], %1;" ::"r"(bar),
+            "h"(both)
+            : "memory");
+    }
+}
+
+// 32 (or 16) accumulator columns of this lane and their maximum, in one
+// tcgen05.ld.red; completed by tmem_wait_ld_max.
+__device__ __forceinline__ void tmem_ldmax32_async(uint32_t taddr, uint32_t (&v)[32], float& mx) {
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "%32, [%33];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31]), "=f"(mx)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ldmax16_async(uint32_t taddr, uint32_t (&v)[32], float& mx) {
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x16.max.f32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, %16, [%17];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=f"(mx)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld_max(uint32_t (&v)[32], float& mx) {
+    asm volatile(
+        "tcgen05.wait::ld.sync.aligned;"
+        : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+          "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]),
+          "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]),
+          "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+          "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]),
+          "+r"(v[31]), "+f"(mx)
+        :
+        : "memory");
+}
+
 // ---- CTA-pair helpers (cluster of two) ----------------------------------
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;
@@ -365,12 +453,12 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                                                  STAGING_BYTES + UBOUND_BYTES);
     uint64_t* full = bars;                       // [MAX_STAGES]
     uint64_t* empty = bars + MAX_STAGES;         // [MAX_STAGES]
-    uint64_t* acc_full = bars + 2 * MAX_STAGES;      // [2]
-    uint64_t* acc_empty = bars + 2 * MAX_STAGES + 2; // [2]
-    uint64_t* done = bars + 2 * MAX_STAGES + 4;      // [1]
-    uint64_t* q_full = bars + 2 * MAX_STAGES + 5;    // [1] the item's query tile landed
-    uint64_t* q_empty = bars + 2 * MAX_STAGES + 6;   // [1] the item's MMAs completed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 7);
+    uint64_t* acc_full = bars + 2 * MAX_STAGES;            // [NACC]
+    uint64_t* acc_empty = bars + 2 * MAX_STAGES + NACC;    // [NACC]
+    uint64_t* done = bars + 2 * MAX_STAGES + 2 * NACC;     // [1]
+    uint64_t* q_full = done + 1;    // [1] the item's query tile landed
+    uint64_t* q_empty = done + 2;   // [1] the item's MMAs completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 3);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
     int* cur_item = abort_flag + 1;   // item the epilogue is on
     int* epi_done = abort_flag + 2;   // epilogue finished (helper stops)
@@ -378,7 +466,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     int* peer_fills = abort_flag + 4; // CG = 2: the same count of the other CTA
     int* qfills = abort_flag + 5;     // query tiles this CTA's producer loaded
     int* peer_qfills = abort_flag + 6;
-    static_assert((2 * MAX_STAGES + 7) * 8 + 4 + 7 * 4 <= 256, "barriers and flags");
+    static_assert((2 * MAX_STAGES + 2 * NACC + 3) * 8 + 4 + 7 * 4 <= 256, "barriers and flags");
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // CTA pair: rank 0 issues the MMAs; both run every other role.
@@ -429,7 +517,7 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < NACC; ++b) {
             mbar_init(&acc_full[b], 1);
             mbar_init(&acc_empty[b], CG * EPI_WARPS);  // one arrival per epilogue warp
         }
@@ -570,9 +658,19 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // the instruction reads the same offsets in the peer CTA (and
             // the scale factors at the same TMEM columns).
             const uint32_t sfa = tmem_base + SF_COL, sfb = tmem_base + SF_COL + 8u;
-            const uint32_t qa0 = smem_u32(qtile), sb0 = smem_u32(stages);
-            int s = 0, tt = 0, qi = 0;
-            uint32_t ph = 0;
+            // Ring positions kept as the values the instructions take: the
+            // stage's barrier addresses and B descriptor, the accumulator's
+            // TMEM address and barrier addresses (a descriptor's start
+            // address is its low field, so offsets add to it directly).
+            const uint32_t full0 = smem_u32(full), empty0 = smem_u32(empty);
+            const uint32_t accf0 = smem_u32(acc_full), acce0 = smem_u32(acc_empty);
+            const uint64_t adesc0 = sw128_desc(smem_u32(qtile)), bdesc0 = sw128_desc(smem_u32(stages));
+            constexpr uint64_t A_CHUNK16 = A_STAGE_BYTES >> 4, B_STAGE16 = STAGE_BYTES >> 4;
+            constexpr uint64_t KSTEP16 = KSTEP >> 4;
+            int s = 0, ab = 0, qi = 0;
+            uint32_t ph = 0, aph = 0;  // stage and accumulator ring phases
+            uint32_t fb = full0, eb = empty0, afb = accf0, aeb = acce0, dt = tmem_base;
+            uint64_t bd = bdesc0;
             bool ok = true;
             // One item's tiles with the chunk loop unrolled for its chunk
             // count: the issuing thread's control flow between MMAs costs
@@ -581,36 +679,66 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             // N = 240, unrolled 120, the instruction's own), so a tile's
             // MMAs, waits and commits are straight-line code; a wait that is
             // not already complete goes to the bounded slow path.
+            // The tensor pipe queues only a few instructions, so the issuing
+            // thread's own work between a chunk's instructions (a barrier
+            // test costs ~90 clocks) idles it unless that work overlaps
+            // queued instructions: the barrier of the next chunk (and, in a
+            // tile's last chunk, the next accumulator's) is tested between
+            // the chunk's second and third instructions, without blocking;
+            // only a test that failed is followed by a (bounded) wait, after
+            // the chunk's commit.
             auto issue_item = [&](auto kch_c, int ntiles) {
                 constexpr int KCH = decltype(kch_c)::value;
+                constexpr int KSTEPS = KCHUNK / KSTEP;
+                static_assert(KSTEPS == 4, "two instructions on either side of the look-ahead");
                 if (!mbar_wait_or_abort(q_full, (uint32_t)(qi & 1), abort_flag)) return false;
-                for (int t = 0; t < ntiles; ++t, ++tt) {
-                    const int b = tt & 1;
-                    const uint32_t use = (uint32_t)(tt >> 1);
-                    if (!mbar_try_wait(&acc_empty[b], (use & 1u) ^ 1u) &&
-                        !mbar_wait_or_abort(&acc_empty[b], (use & 1u) ^ 1u, abort_flag))
+                if (ntiles > 0) {
+                    if (!mbar_try_wait_u32(aeb, aph ^ 1u) &&
+                        !mbar_wait_or_abort(&acc_empty[ab], aph ^ 1u, abort_flag))
+                        return false;
+                    if (!mbar_try_wait_u32(fb, ph) && !mbar_wait_or_abort(&full[s], ph, abort_flag))
                         return false;
                     tc_fence_after();
-                    const uint32_t dt = tmem_base + (uint32_t)(b * MMA_N);
+                }
+                for (int t = 0; t < ntiles; ++t) {
+                    const bool more = t + 1 < ntiles;
+                    bool acc_ready = true;  // the next tile's accumulator, tested in the last chunk
+                    const bool awrap = ab + 1 == NACC;
+                    const uint32_t naeb = awrap ? acce0 : aeb + 8u;
+                    const uint32_t naph = aph ^ (awrap ? 1u : 0u);
 #pragma unroll
                     for (int kc = 0; kc < KCH; ++kc) {
-                        if (!mbar_try_wait(&full[s], ph) &&
-                            !mbar_wait_or_abort(&full[s], ph, abort_flag))
-                            return false;
-                        tc_fence_after();
-                        const uint32_t sa = qa0 + (uint32_t)(kc * A_STAGE_BYTES);
-                        const uint32_t sb = sb0 + (uint32_t)(s * STAGE_BYTES);
-#pragma unroll
-                        for (int kk = 0; kk < KCHUNK / KSTEP; ++kk) {
-                            mma_f4<CG>(dt, sw128_desc(sa + kk * KSTEP), sw128_desc(sb + kk * KSTEP),
-                                       sfa, sfb, (kc > 0 || kk > 0) ? 1u : 0u);
-                        }
-                        mma_commit_all<CG>(&empty[s]);
+                        const bool next = kc + 1 < KCH || more;  // a chunk follows in this item
                         const bool wrap = s + 1 == nst;
+                        const uint32_t nfb = wrap ? full0 : fb + 8u;
+                        const uint32_t nph = ph ^ (wrap ? 1u : 0u);
+                        const uint64_t a = adesc0 + (uint64_t)kc * A_CHUNK16;
+                        mma_f4<CG>(dt, a, bd, sfa, sfb, kc > 0 ? 1u : 0u);
+                        mma_f4<CG>(dt, a + KSTEP16, bd + KSTEP16, sfa, sfb, 1u);
+                        bool stage_ready = true;
+                        if (next) stage_ready = mbar_test_wait_u32(nfb, nph);
+                        if (kc == KCH - 1 && more) acc_ready = mbar_test_wait_u32(naeb, naph ^ 1u);
+                        mma_f4<CG>(dt, a + 2 * KSTEP16, bd + 2 * KSTEP16, sfa, sfb, 1u);
+                        mma_f4<CG>(dt, a + 3 * KSTEP16, bd + 3 * KSTEP16, sfa, sfb, 1u);
+                        mma_commit_all_u32<CG>(eb);
                         s = wrap ? 0 : s + 1;
-                        ph ^= wrap ? 1u : 0u;
+                        ph = nph;
+                        fb = nfb;
+                        eb = wrap ? empty0 : eb + 8u;
+                        bd = wrap ? bdesc0 : bd + B_STAGE16;
+                        if (next && !stage_ready && !mbar_wait_or_abort(&full[s], ph, abort_flag))
+                            return false;
+                        if (kc < KCH - 1) tc_fence_after();
                     }
-                    mma_commit_all<CG>(&acc_full[b]);
+                    mma_commit_all_u32<CG>(afb);
+                    ab = awrap ? 0 : ab + 1;
+                    aph = naph;
+                    afb = awrap ? accf0 : afb + 8u;
+                    aeb = naeb;
+                    dt = awrap ? tmem_base : dt + (uint32_t)MMA_N;
+                    if (more && !acc_ready && !mbar_wait_or_abort(&acc_empty[ab], aph ^ 1u, abort_flag))
+                        return false;
+                    tc_fence_after();
                 }
                 // the query tile is free once the item's MMAs complete
                 mma_commit_all<CG>(q_empty);
@@ -639,11 +767,9 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;
         const int m = quarter * 32 + lane;  // TMEM lane = query row in the tile
-        int tt = 0;  // accumulator tiles consumed so far (all items)
+        int ab = 0;        // accumulator ring position and phase (runs on across items)
+        uint32_t aph = 0;
         bool ok = true;
-        // accumulator release: the leader's barrier (in the other CTA for rank 1)
-        const uint32_t acc_empty0 = CG == 2 ? peer_addr(&acc_empty[0], 0u) : 0u;
-        const uint32_t acc_empty1 = CG == 2 ? peer_addr(&acc_empty[1], 0u) : 0u;
         for (int item = worker; item < nitems && ok; item += nworkers) {
         const Item w = item_of(item);
         const MmaArgs& a = args_of(w.b);
@@ -692,12 +818,10 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             sc = 0;
             if (hs == k) dtau = (float)(a.x - (int)(heap[m] >> LOCAL_BITS));
         };
-        for (int t = 0; t < ntiles; ++t, ++tt) {
-            const int b = tt & 1;
-            const uint32_t use = (uint32_t)(tt >> 1);
+        for (int t = 0; t < ntiles; ++t) {
             // one lane waits, the warp follows it (keeps the warp converged)
             int got = 1;
-            if (lane == 0) got = mbar_wait_or_abort(&acc_full[b], use & 1u, abort_flag);
+            if (lane == 0) got = mbar_wait_or_abort(&acc_full[ab], aph, abort_flag);
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) {
                 ok = false;
@@ -713,25 +837,22 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 }
             }
             const int64_t tile_row = row0 + (int64_t)t * MMA_N;
-            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * MMA_N);
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(ab * MMA_N);
             // One 32-column group already in registers: stage the lanes'
             // candidates (flushing first if a lane's staging could overflow).
-            auto group = [&](const uint32_t (&v)[32], int c) {
-                // maxima of the 8 sub-groups of 4 columns, then of the group
+            // mx: the group's maximum, from the load itself.
+            auto group = [&](const uint32_t (&v)[32], float mx, int c) {
+                float thr = fmaxf(dtau, dglob);
+                if (!__any_sync(0xffffffffu, valid_q && mx > thr)) return;
+                // maxima of the 8 sub-groups of 4 columns
                 float sm[8];
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     sm[i] = fmaxf(fmax3(__uint_as_float(v[4 * i]), __uint_as_float(v[4 * i + 1]),
                                         __uint_as_float(v[4 * i + 2])),
                                   __uint_as_float(v[4 * i + 3]));
-                const float mx = fmax3(fmax3(sm[0], sm[1], sm[2]), fmax3(sm[3], sm[4], sm[5]),
-                                       fmaxf(sm[6], sm[7]));
-                float thr = fmaxf(dtau, dglob);
-                if (!__any_sync(0xffffffffu, valid_q && mx > thr)) return;
-                // columns of this group inside the tile (the last group has
-                // MMA_N - 224 = 16; the rest of its load is another
-                // accumulator's or the scale factors) and inside the slice
-                // (the last tile is ragged)
+                // columns of this group inside the tile and inside the
+                // slice (the last tile is ragged)
                 const int64_t left = min(row_end - (tile_row + c * 32), (int64_t)(MMA_N - 32 * c));
                 const int lim = !valid_q ? 0 : (left >= 32 ? 32 : (left > 0 ? (int)left : 0));
                 uint32_t my8 = 0;  // this lane's 4-column sub-groups with a candidate
@@ -768,28 +889,47 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                 }
             };
             // Two register buffers: the load of the next group is in flight
-            // while the current one is examined.
+            // while the current one is examined.  A last group narrower than
+            // 32 columns is loaded 16 wide, so that its maximum covers only
+            // this tile's columns.
+            auto load_group = [&](int c, uint32_t (&v)[32], float& mx) {
+                if (MMA_N % 32 != 0 && c == EPI_GROUPS - 1)
+                    tmem_ldmax16_async(tbase + (uint32_t)(c * 32), v, mx);
+                else
+                    tmem_ldmax32_async(tbase + (uint32_t)(c * 32), v, mx);
+            };
+            static_assert(MMA_N % 32 == 0 || MMA_N % 32 == 16, "last group 16 or 32 wide");
             uint32_t va[32], vb[32];
+            float ma = 0.f, mb = 0.f;
             __syncwarp();
-            tmem_ld32_async(tbase, va);
-            tmem_wait_ld(va);
+            load_group(0, va, ma);
+            tmem_wait_ld_max(va, ma);
 #pragma unroll 1
             for (int c = 0; c < EPI_GROUPS; c += 2) {
+                const bool two = c + 1 < EPI_GROUPS;  // an odd group count ends on one group
                 __syncwarp();
-                tmem_ld32_async(tbase + (uint32_t)((c + 1) * 32), vb);
-                group(va, c);
-                __syncwarp();
-                tmem_wait_ld(vb);
-                if (c + 2 < EPI_GROUPS) tmem_ld32_async(tbase + (uint32_t)((c + 2) * 32), va);
-                group(vb, c + 1);
-                __syncwarp();
-                if (c + 2 < EPI_GROUPS) tmem_wait_ld(va);
+                if (two) load_group(c + 1, vb, mb);
+                group(va, ma, c);
+                if (two) {
+                    __syncwarp();
+                    tmem_wait_ld_max(vb, mb);
+                    if (c + 2 < EPI_GROUPS) load_group(c + 2, va, ma);
+                    group(vb, mb, c + 1);
+                    __syncwarp();
+                    if (c + 2 < EPI_GROUPS) tmem_wait_ld_max(va, ma);
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) {
-                if constexpr (CG == 1) mbar_arrive(&acc_empty[b]);
-                else mbar_arrive_cluster(b ? acc_empty1 : acc_empty0);
+                // accumulator release: the leader's barrier (in the other CTA for rank 1)
+                if (CG == 1 || rank == 0) mbar_arrive(&acc_empty[ab]);
+                else mbar_arrive_cluster(peer_addr(&acc_empty[ab], 0u));
+            }
+            {
+                const bool awrap = ab + 1 == NACC;
+                ab = awrap ? 0 : ab + 1;
+                aph ^= awrap ? 1u : 0u;
             }
             // heap updates run after the accumulator is released, overlapping
             // the next tile's MMAs
