@@ -341,10 +341,11 @@ size_t knn_ws_bound(int64_t nq, int64_t ns, int d, int k, int path, bool convert
 int mma_active_queries(int k);
 // tiles_per_item > 0: slices of about that many 240-row database tiles (the
 // tile shape of the fused multi-batch scan) instead of whole waves.
-// allow_cap: for k > 128, keep 128 keys per (query, slice) -- every query
-// lane of a tile active -- when the slices are many enough that a slice
-// rarely holds more than 64 of a query's k nearest (nslices x 64 >= k); a
-// repair pass then makes the result exact (run_mma_knn).
+// allow_cap: keep kl < k keys per (query, slice) -- kl the smallest power of
+// two >= 16 with kl x nslices >= 4k, at most 128 (every query lane of a tile
+// active) -- when the slices are many enough that a slice rarely holds more
+// than kl / 2 of a query's k nearest (nslices x kl / 2 >= k); a repair pass
+// then makes the result exact (run_mma_knn).
 MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
                       int tiles_per_item = 0, bool allow_cap = false);
 

@@ -1355,9 +1355,17 @@ MmaPlan plan_mma_scan(int64_t nq, int64_t ns, int d, int k, bool convert_db,
                      p.hist_bytes;
         return p;
     };
-    if (allow_cap && k > MMA_M && tiles_per_item == 0) {
-        const MmaPlan c = build(MMA_M);
-        if ((int64_t)c.nslices * (MMA_M / 2) >= k) return c;
+    // Capped lists: each slice keeps its kl best keys, kl the smallest power
+    // of two >= 16 with kl x nslices >= 4k (a slice holds k / nslices of a
+    // query's k nearest on average; the repair pass rescans the rare slice
+    // that may have held more).  A smaller heap settles its threshold on
+    // fewer rows and is cheaper to update, which is most of the scan's
+    // epilogue work while the thresholds are loose.
+    if (allow_cap && tiles_per_item == 0) {
+        const MmaPlan c = build(std::min(k, MMA_M));  // slicing does not depend on kl <= 128
+        int kl = 16;
+        while (kl < MMA_M && (int64_t)kl * c.nslices < 4 * (int64_t)k) kl *= 2;
+        if (kl < k && (int64_t)c.nslices * (kl / 2) >= k) return build(kl);
     }
     return build(k);
 }

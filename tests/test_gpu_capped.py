@@ -1,5 +1,6 @@
-"""The tensor-core scan with capped lists (k > 128: 128 keys per query and
-slice, every query lane active) against the oracle, including databases
+"""The tensor-core scan with capped lists (kl < k keys per query and slice:
+the smallest power of two >= 16 with kl x slices >= 4k, at most 128) against
+the oracle, including databases
 ordered so that a query's k nearest rows are contiguous -- they then fall
 into one or two slices, far more than a capped list keeps, and only the
 repair pass (a rescan of those slices) can make the result exact."""
@@ -25,7 +26,7 @@ def _knn(evp, Vq, Vs, d, x, k, dev):
     return ids.cpu().numpy(), dist.cpu().numpy()
 
 
-@pytest.mark.parametrize("nq,k", [(8, 700), (200, 300), (3, 1024)])
+@pytest.mark.parametrize("nq,k", [(8, 700), (200, 300), (3, 1024), (200, 100), (40, 33)])
 def test_contiguous_neighbours_are_repaired(evp_lib, dev, nq, k):
     d, x, ns = 384, 128, 20_000
     U = synth.mixture_numpy(ns, d, n_centres=32, stream=900)
@@ -41,7 +42,7 @@ def test_contiguous_neighbours_are_repaired(evp_lib, dev, nq, k):
     assert np.array_equal(np.sort(ids[0]), np.arange(k))   # the contiguous block itself
 
 
-@pytest.mark.parametrize("k", [129, 500, 1000])
+@pytest.mark.parametrize("k", [33, 100, 129, 500, 1000])
 def test_random_order_large_k(evp_lib, dev, k):
     d, x, ns, nq = 256, 171, 60_000, 100
     U = synth.mixture_numpy(ns, d, n_centres=64, stream=910)
