@@ -766,7 +766,8 @@ def main():
     evp.timing_enable(False)
     per_kernel = {name: evp.timing_read(name) for name in
                   ("encode", "quantize", "scan_init", "scan_popc", "unpack_fp4", "scan_mma",
-                   "scan_mma_packed", "scan_i8q", "scan_sparse", "final_merge", "rerank")}
+                   "scan_mma_packed", "scan_i8q", "scan_sparse", "final_merge", "scan_repair",
+                   "rerank")}
     evp.check_status(st, "timed kernels")
 
     # ---- end to end through the API with host buffers (pinned)

@@ -318,6 +318,19 @@ __device__ __forceinline__ void tmem_ldmax16_async(uint32_t taddr, uint32_t (&v)
           "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=f"(mx)
         : "r"(taddr));
 }
+// Orders later uses of v and mx after a tcgen05.wait::ld already issued
+// (which waits for every load of the thread): no instruction of its own.
+__device__ __forceinline__ void tmem_loaded(uint32_t (&v)[32], float& mx) {
+    asm volatile(""
+        : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]),
+          "+r"(v[7]), "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]),
+          "+r"(v[13]), "+r"(v[14]), "+r"(v[15]), "+r"(v[16]), "+r"(v[17]), "+r"(v[18]),
+          "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]), "+r"(v[24]),
+          "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]),
+          "+r"(v[31]), "+f"(mx)
+        :
+        : "memory");
+}
 __device__ __forceinline__ void tmem_wait_ld_max(uint32_t (&v)[32], float& mx) {
     asm volatile(
         "tcgen05.wait::ld.sync.aligned;"
@@ -888,10 +901,12 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     }
                 }
             };
-            // Two register buffers: the load of the next group is in flight
-            // while the current one is examined.  A last group narrower than
-            // 32 columns is loaded 16 wide, so that its maximum covers only
-            // this tile's columns.
+            // The groups' maxima are taken in batches of four loads and one
+            // wait (the load latency, not the comparison, dominates a group
+            // whose maximum clears nothing); a group in which some lane has
+            // a candidate is loaded again and examined from one register
+            // buffer.  A last group narrower than 32 columns is loaded 16
+            // wide, so that its maximum covers only this tile's columns.
             auto load_group = [&](int c, uint32_t (&v)[32], float& mx) {
                 if (MMA_N % 32 != 0 && c == EPI_GROUPS - 1)
                     tmem_ldmax16_async(tbase + (uint32_t)(c * 32), v, mx);
@@ -899,24 +914,35 @@ scan_mma_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
                     tmem_ldmax32_async(tbase + (uint32_t)(c * 32), v, mx);
             };
             static_assert(MMA_N % 32 == 0 || MMA_N % 32 == 16, "last group 16 or 32 wide");
-            uint32_t va[32], vb[32];
-            float ma = 0.f, mb = 0.f;
-            __syncwarp();
-            load_group(0, va, ma);
-            tmem_wait_ld_max(va, ma);
+            constexpr int BATCH = 4;
 #pragma unroll 1
-            for (int c = 0; c < EPI_GROUPS; c += 2) {
-                const bool two = c + 1 < EPI_GROUPS;  // an odd group count ends on one group
+            for (int c0 = 0; c0 < EPI_GROUPS; c0 += BATCH) {
+                uint32_t b0[32], b1[32], b2[32], b3[32];
+                float m0 = -INFINITY, m1 = -INFINITY, m2 = -INFINITY, m3 = -INFINITY;
+                const int nb = min(BATCH, EPI_GROUPS - c0);  // warp-uniform
                 __syncwarp();
-                if (two) load_group(c + 1, vb, mb);
-                group(va, ma, c);
-                if (two) {
+                load_group(c0, b0, m0);
+                if (nb > 1) load_group(c0 + 1, b1, m1);
+                if (nb > 2) load_group(c0 + 2, b2, m2);
+                if (nb > 3) load_group(c0 + 3, b3, m3);
+                tmem_wait_ld_max(b0, m0);
+                tmem_loaded(b1, m1);
+                tmem_loaded(b2, m2);
+                tmem_loaded(b3, m3);
+                const float thr = fmaxf(dtau, dglob);
+                const uint32_t flag = !valid_q ? 0u
+                                               : (m0 > thr ? 1u : 0u) | (m1 > thr ? 2u : 0u) |
+                                                     (m2 > thr ? 4u : 0u) | (m3 > thr ? 8u : 0u);
+                uint32_t wflag = __reduce_or_sync(0xffffffffu, flag);
+                while (wflag) {
+                    const int i = __ffs(wflag) - 1;
+                    wflag &= wflag - 1u;
+                    uint32_t vx[32];
+                    float mx;
                     __syncwarp();
-                    tmem_wait_ld_max(vb, mb);
-                    if (c + 2 < EPI_GROUPS) load_group(c + 2, va, ma);
-                    group(vb, mb, c + 1);
-                    __syncwarp();
-                    if (c + 2 < EPI_GROUPS) tmem_wait_ld_max(va, ma);
+                    load_group(c0 + i, vx, mx);
+                    tmem_wait_ld_max(vx, mx);
+                    group(vx, mx, c0 + i);
                 }
             }
             tc_fence_before();
