@@ -148,16 +148,16 @@ MEASURED_TRAFFIC = {
     # histograms, independent of the rows) as captured.
     # profiles/scan_mma_10Mx768_b1024_launches.md
     ("scan_mma", 10_000_000, 768, 1024, 100): {
-        "bytes": 386_433_280 * 10 + 3_969_280,
-        "sources_sha256": "1f5e24cb456b30bd7cf5461230a2c284c8d4bdb8774ade8d495e1565718ba0b6"},
+        "bytes": 386_409_728 * 10 + 3_898_368,
+        "sources_sha256": "ee5f93933c384e70a53a398f1ade0422c5ae0e7622299cfda59d59ae8a9e8f82"},
     # profiles/scan_popc_1Mx768_b1_ncu.md
     ("scan_popc", 10_000_000, 768, 1, 100): {
         "bytes": 192_033_024 * 10 + 3_496_192,
-        "sources_sha256": "c8fee449e965c0380796eff6746723fcfc4d52b06a4c7d71314d8288f6dab996"},
+        "sources_sha256": "cdf7029f81db7af20486a0732bd77ca154d54c6067ec22f9d701f7fcae8b85bf"},
     # profiles/scan_mma_packed_10Mx768_b16.md
     ("scan_mma_packed", 10_000_000, 768, 16, 100): {
         "bytes": 194_052_096 * 10 + 9_144_832,
-        "sources_sha256": "9bc6bbd1ea71a3206d7b033908286945a01661819dabb3283c55470b58cc0acd"},
+        "sources_sha256": "f6f8798da020b1700b119d945568766194ea2a950212a4bdf4c95d4ea2e665e5"},
 }
 
 
