@@ -149,7 +149,7 @@ MEASURED_TRAFFIC = {
     # profiles/scan_mma_10Mx768_b1024_launches.md
     ("scan_mma", 10_000_000, 768, 1024, 100): {
         "bytes": 386_409_728 * 10 + 3_898_368,
-        "sources_sha256": "ee5f93933c384e70a53a398f1ade0422c5ae0e7622299cfda59d59ae8a9e8f82"},
+        "sources_sha256": "0ded91804e7e82397f9acc8e74bb217f2f7ef915086e8450a78a0356e3f501a6"},
     # profiles/scan_popc_1Mx768_b1_ncu.md
     ("scan_popc", 10_000_000, 768, 1, 100): {
         "bytes": 192_033_024 * 10 + 3_496_192,

@@ -30,24 +30,27 @@
 //   warp 6      threshold helper: recomputes each query's union bound (below)
 //               from the workspace histogram and publishes it in shared memory;
 //   warps 2-5   epilogue: tcgen05.ld of the accumulator (thread = TMEM lane
-//               = query), Delta from D, and a private max-heap of the k best
-//               (Delta/2 << 20 | row-in-slice) keys in shared memory.  A row
-//               is a candidate only if its D beats the heap root (rows arrive
-//               in ascending index order, so an equal Delta never displaces)
-//               and is not worse than the union bound: every key any slice
-//               of the query inserts is counted in a per-query Delta
-//               histogram in the workspace, and the k-th smallest counted
-//               Delta bounds the answer for all slices.
-//               Each 32-column TMEM load is reduced to eight 4-column maxima
-//               and their maximum (three-input max); a warp skips the group
-//               when no lane has a candidate, and otherwise examines only the
-//               4-column sub-groups in which some lane has one.  Candidates
-//               go to a per-thread staging buffer that the warp inserts into
-//               the heaps together when a lane's buffer could overflow, so
-//               heap updates of different lanes do not serialise.
+//               = query), Delta from D, and a private max-heap of the kl
+//               best (Delta/2 << 20 | row-in-slice) keys in shared memory.
+//               A row is a candidate only if its D beats the heap root (rows
+//               arrive in ascending index order, so an equal Delta never
+//               displaces) and is not worse than the union bound: every key
+//               any slice of the query inserts is counted in a per-query
+//               Delta histogram in the workspace, and the k-th smallest
+//               counted Delta bounds the answer for all slices.
+//               The maxima of 32-column groups come from tcgen05.ld.red,
+//               four loads per wait; a warp skips a group when no lane has a
+//               candidate, and otherwise loads it again and examines only
+//               the 4-column sub-groups in which some lane has one.
+//               Candidates go to a per-thread staging buffer that the warp
+//               inserts into the heaps together when a lane's buffer could
+//               overflow, so heap updates of different lanes do not
+//               serialise.
 // The Delta matrix is never written to memory.  Per (query, slice) sorted
-// lists go to the workspace and the per-query merge of the popcount path
-// combines them.  Every mbarrier wait is bounded (2 s); on expiry the CTA
+// lists of kl keys go to the workspace and the per-query merge of the
+// popcount path combines them; with kl < k (capped lists) a check of every
+// list's tail against the merged k-th key, and a rescan of the rare slice
+// that may have held more, keep the result exact.  Every mbarrier wait is bounded (2 s); on expiry the CTA
 // reports EVP_ERR_TIMEOUT, raises an abort flag in itself and its pair
 // peer (every other wait then gives up at once), waits (bounded) for the
 // copies and MMAs already issued to complete, and frees TMEM.
