@@ -249,8 +249,13 @@ int32_t ternary_knn_static(const uint64_t* Q, int64_t nq, const uint64_t* S, int
  *                  side: the codes are expanded to half a byte per element
  *                  (in the workspace when S is given packed, or once for a
  *                  database created with EVP_DB_TENSOR_COPY).
- *                  A 128-query tile serves all 128 queries for k <= 128 and
- *                  fewer (64, 32, 16) for larger k; best for large batches.
+ *                  Each database slice keeps kl keys per query: kl < k (a
+ *                  power of two, 16-128) when the slices are many enough,
+ *                  with a check of every list's tail after the merge and a
+ *                  rescan of the rare slice that may have held more (the
+ *                  result stays exact); otherwise kl = k, and for k > 128
+ *                  a 128-query tile then serves fewer queries (64, 32, 16).
+ *                  Best for large batches.
  *   EVP_PATH_MMA_PACKED  tensor-core scan with the database as the 128-row
  *                  side: reads the packed codes once per 64 queries and
  *                  unpacks each tile on chip into tensor memory; needs
